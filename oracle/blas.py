@@ -1,0 +1,121 @@
+"""The four BLAS programs of arXiv 1502.02389, Fig. 5, written in the
+high-level patterns and evaluated by the FP64 interpreter.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+    scal(a, x)          = map(mult(a), x)
+    asum(x)             = reduce(add, 0) . map(abs, x)
+    dot(x, y)           = reduce(add, 0) . map(mult) . zip(x, y)
+    gemv(A, x, y, a, b) : z = map(scal(a) . dot(x), A)
+                          map(add) . zip(z, scal(b, y))
+
+gemv computes y = a*A*x + b*y "as defined by the BLAS library" (Sec. 5.1).
+Two readings are taken where Fig. 5 leaves room:
+  * map(scal(a) . dot(x), A) yields one length-1 array per row (every value
+    is an array, Sec. 3), so z is that result joined to length M before the
+    zip with y;
+  * with b = 0 the BLAS definition does not read y, so y' = a*A*x and a NaN
+    in y does not propagate.
+
+The parity tolerance for an fp32 result r against the FP64 value v of a sum
+of terms t_i is |r - v| <= 4 * 2^-24 * max(1, ceil(log2 n)) * sum|t_i|
+(u = 2^-24 is the unit roundoff of fp32).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .patterns import (C, Join, Map, Reduce, Zip, ZipWith, abs_, add, evaluate,
+                       mult, mult_by)
+
+U_FP32 = 2.0 ** -24
+
+
+def scal_expr(a):
+    return Map(mult_by(a))
+
+
+def asum_expr():
+    return C(Reduce(add, 0), Map(abs_))
+
+
+def dot_expr():
+    return C(Reduce(add, 0), Map(mult), Zip())
+
+
+def gemv_z_expr(a):
+    """z = join . map(scal(a) . dot(x), A); dot(x) zips the captured x with
+    each row of A."""
+    dot_x = C(Reduce(add, 0), Map(mult), ZipWith("x"))
+    return C(Join(), Map(C(scal_expr(a), dot_x)))
+
+
+def gemv_y_expr():
+    """y' = map(add) . zip(z, scal(b, y))."""
+    return C(Map(add), Zip())
+
+
+def scal(a, x, mode="f64"):
+    return evaluate(scal_expr(a), np.asarray(x), mode)
+
+
+def asum(x, mode="f64") -> float:
+    x = np.asarray(x)
+    if x.size == 0:
+        return 0.0  # reduce of an empty array is z (Table 1; Sec. 3.2)
+    return float(evaluate(asum_expr(), x, mode)[0])
+
+
+def dot(x, y, mode="f64") -> float:
+    x, y = np.asarray(x), np.asarray(y)
+    if x.size == 0:
+        return 0.0
+    return float(evaluate(dot_expr(), (x, y), mode)[0])
+
+
+def gemv(A, x, y, alpha, beta, mode="f64"):
+    """y' = alpha*A*x + beta*y (row-major A of shape (M, N))."""
+    A, x, y = np.asarray(A), np.asarray(x), np.asarray(y)
+    M, N = A.shape
+    if M == 0:
+        return np.zeros(0)
+    if N == 0:
+        z = np.zeros(M)
+    else:
+        z = evaluate(gemv_z_expr(alpha), A, mode, env={"x": x})
+    if beta == 0:
+        return np.asarray(z, dtype=np.float64)
+    by = scal(beta, y, mode)
+    return evaluate(gemv_y_expr(), (z, by), mode)
+
+
+# ---------------------------------------------------------------------------
+# tolerance
+# ---------------------------------------------------------------------------
+def depth(n: int) -> int:
+    return max(1, math.ceil(math.log2(n))) if n > 1 else 1
+
+
+def tolerance(n: int, sum_abs_terms: float) -> float:
+    """4 * u_fp32 * max(1, ceil(log2 n)) * sum|terms|."""
+    return 4.0 * U_FP32 * depth(n) * float(sum_abs_terms)
+
+
+def asum_terms(x) -> float:
+    return float(np.sum(np.abs(np.asarray(x, np.float64))))
+
+
+def dot_terms(x, y) -> float:
+    return float(np.sum(np.abs(np.asarray(x, np.float64) * np.asarray(y, np.float64))))
+
+
+def gemv_row_terms(A, x, y, alpha, beta):
+    """|alpha| * sum_j |A_ij x_j| + |beta * y_i| per row."""
+    A = np.asarray(A, np.float64)
+    x = np.asarray(x, np.float64)
+    t = abs(alpha) * (np.abs(A) @ np.abs(x))
+    if beta != 0:
+        t = t + np.abs(beta * np.asarray(y, np.float64))
+    return t

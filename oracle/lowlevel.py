@@ -1,0 +1,204 @@
+"""Low-level expressions: the ones the paper prints (Fig. 2b, Fig. 8, Fig. 9)
+and the parametrised expression each GPU kernel variant evaluates.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+The kernel-variant expressions are written only with the patterns of
+Table 1 and Table 2 (plus ``PadTo`` for the neutral padding of a ragged
+tail).  Evaluated in the interpreter's fp32 mode they state, operation by
+operation, the arithmetic of an fp32 kernel whose CTAs are workgroups and
+whose threads are local threads: per-thread sequential folds
+(reduce-seq), lane-wise vectors (asVector / vect), coalescing order
+(reorder-stride), halving trees (iterate over split-2), and an FP64 final
+combine.  A kernel built from the same expression must agree bit for bit.
+"""
+from __future__ import annotations
+
+import math
+
+from .patterns import (AsScalar, AsVector, C, Id, Iterate, Join, Map, MapLocal,
+                       MapSeq, MapWorkgroup, PadTo, PartRed, Reduce, ReduceSeq,
+                       Reorder, ReorderStride, Split, ToGlobal, ToLocal, Vect, Zip,
+                       ZipWith, abs_, absAndPlus, add, add64, fold, id_, mul3,
+                       mult, mult_by, to_f32, to_f64)
+
+
+# ============================================================================
+# Fig. 2b -- vectorScal = join . map-workgroup(asScalar . map-local(
+#            vectorize-4(mul3)) . asVector-4) . split-1024
+# ============================================================================
+def fig2b_vector_scal():
+    return C(Join(),
+             MapWorkgroup(C(AsScalar(), MapLocal(Vect(4, mul3)), AsVector(4))),
+             Split(1024))
+
+
+# ============================================================================
+# Fig. 8 -- the fused asum derivation, equations (1) to (8), as printed
+# (eq. (8) closes the parenthesis the figure leaves open)
+# ============================================================================
+def fig8_equations(n: int):
+    PR = PartRed(add, 0)
+    R = Reduce(add, 0)
+    return [
+        C(R, Map(abs_)),                                                    # (1)
+        C(R, Join(), Map(PR), Split(n), Map(abs_)),                         # (2)
+        C(R, Join(), Map(PR), Split(n), Join(), Map(Map(abs_)), Split(n)),  # (3)
+        C(R, Join(), Map(PR), Map(Map(abs_)), Split(n)),                    # (4)
+        C(R, Join(), Map(C(PR, Map(abs_))), Split(n)),                      # (5)
+        C(R, Join(), Map(C(PR, MapSeq(abs_))), Split(n)),                   # (6)
+        C(R, Join(), Map(C(ReduceSeq(add, 0), MapSeq(abs_))), Split(n)),    # (7)
+        C(R, Join(), Map(ReduceSeq(absAndPlus, 0)), Split(n)),              # (8)
+    ]
+
+
+# ============================================================================
+# Fig. 9 -- device-specific asum expressions.  Fig. 9 writes reorder-stride
+# without its stride; it is read as s = len / n_next, n_next being the size
+# of the split that follows (s = 128 in (a), s = 256 in (b)).  The outer
+# reduce-seq carries no arguments in the figure; they are (add, 0).
+# "absAnd+" in (c) is absAndPlus.
+# ============================================================================
+def fig9a_nvidia():
+    return C(
+        ReduceSeq(add, 0), Join(),
+        MapWorkgroup(C(
+            Join(), ToGlobal(MapLocal(MapSeq(id_))), Split(1),
+            Iterate(7, C(Join(), MapLocal(ReduceSeq(add, 0)), Split(2))),
+            Join(), ToLocal(MapLocal(ReduceSeq(absAndPlus, 0))), Split(2048),
+            ReorderStride(n=2048))),
+        Split(262144))
+
+
+def fig9b_amd():
+    v4 = lambda f: Vect(4, f)  # noqa: E731
+    return C(
+        ReduceSeq(add, 0), Join(), AsScalar(),
+        MapWorkgroup(C(
+            Join(), ToGlobal(MapLocal(MapSeq(v4(id_)))), Split(1),
+            Iterate(8, C(Join(), MapLocal(ReduceSeq(v4(add), 0)), Split(2))),
+            Join(), ToLocal(MapLocal(ReduceSeq(v4(absAndPlus), 0))), Split(2),
+            ReorderStride(n=2))),
+        AsVector(4), Split(2048))
+
+
+def fig9c_intel():
+    return C(
+        ReduceSeq(add, 0), Join(), AsScalar(),
+        MapWorkgroup(C(
+            Join(), MapLocal(ReduceSeq(Vect(4, absAndPlus), 0)), Split(8192))),
+        AsVector(4), Split(32768))
+
+
+# ============================================================================
+# Kernel variants
+# ============================================================================
+WARP = 32
+
+
+def halving_tree(plus=add):
+    """One warp-wide halving tree: iterate-5(join . map-local(reduce-seq(+))
+    . split-2 . reorder-stride(n=2)).  Each level pairs element j with
+    element j + len/2, which is what a shuffle-down by len/2 computes."""
+    level = C(Join(), MapLocal(ReduceSeq(plus, 0)), Split(2), ReorderStride(n=2))
+    return Iterate(5, level)
+
+
+def block_tree(threads: int, plus=add):
+    """[threads] -> [1]: a halving tree inside every warp, then the warp
+    results (padded with zeros to one warp) through one more warp tree."""
+    warps = threads // WARP
+    e = C(Join(), Map(halving_tree(plus)), Split(WARP))
+    if warps > 1:
+        e = C(halving_tree(plus), PadTo(WARP), e)
+    return e
+
+
+def _thread_order(threads: int, per_thread: int, J: int, stride: bool):
+    """Vectors of one CTA (its tiles in order, J per thread per tile) ->
+    [threads][per_thread]; thread t takes, tile by tile, vectors
+    t + threads*j (stride) or t*J + j (contiguous chunk)."""
+    if stride:
+        return C(Split(per_thread), ReorderStride(s=threads))
+    return C(Split(per_thread), Join(), ReorderStride(s=threads), Split(J))
+
+
+def final_combine(P: int, ft: int, cast32: bool = True):
+    """[P] fp32 partials -> [1]: thread t of one CTA of ft threads sums
+    partials t, t+ft, ... in FP64, then an FP64 block tree; the result is
+    rounded to fp32 when cast32."""
+    M = max(1, math.ceil(P / ft))
+    body = C(block_tree(ft, add64), Join(),
+             MapLocal(ReduceSeq(add64, 0)), Split(M), ReorderStride(s=ft),
+             PadTo(ft * M), Map(to_f64))
+    if cast32:
+        body = C(Map(to_f32), body)
+    return C(Join(), MapWorkgroup(body), Split(P))
+
+
+def reduce_variant(op: str, n: int, tile: int, vw: int, threads: int, grid: int,
+                   stride: bool = True, cluster: int = 1, ft: int = 256,
+                   cast32: bool = True):
+    """Expression of a fp32 asum/dot kernel variant and the padded input
+    length it expects (the input padded with zeros to that length).
+
+    Tiles of ``tile`` elements go to the ``grid`` CTAs round robin
+    (CTA b takes tiles b, b+grid, ...: reorder-stride^grid at tile level);
+    every thread folds its vectors in order into ``vw`` lane accumulators
+    (reduce-seq over vect^vw(absAndPlus) or of the fused multiply-add
+    fold), adds its lanes in order, then the CTA runs ``block_tree``; with a
+    cluster, ``cluster`` consecutive CTA results are added in rank order;
+    the partials are combined by ``final_combine``."""
+    if op not in ("asum", "dot"):
+        raise ValueError(op)
+    T = max(1, math.ceil(n / tile))
+    K = math.ceil(T / grid)
+    L = grid * K * tile
+    V = tile // vw
+    J = V // threads
+    assert V % threads == 0 and tile % vw == 0 and grid % cluster == 0
+    f = absAndPlus if op == "asum" else fold(add, mult)
+    fr = Vect(vw, f) if vw > 1 else f
+    per_thread = K * J
+    lanes = Id()
+    if vw > 1:
+        lanes = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
+    cta = C(block_tree(threads), lanes, Join(), MapLocal(ReduceSeq(fr, 0)),
+            _thread_order(threads, per_thread, J, stride),
+            AsVector(vw) if vw > 1 else Id())
+    parts = C(Join(), MapWorkgroup(cta), Split(K * tile), Join(),
+              ReorderStride(s=grid), Split(tile), PadTo(L))
+    P = grid
+    if cluster > 1:
+        parts = C(Join(), Map(ReduceSeq(add, 0)), Split(cluster), parts)
+        P = grid // cluster
+    e = C(final_combine(P, ft, cast32), parts)
+    if op == "dot":
+        e = C(e, Zip())
+    return e, L
+
+
+def gemv_row_variant(N: int, vw: int, lanes: int = WARP):
+    """Expression of one row of the gemv kernel: ``lanes`` threads share the
+    row; lane l folds vectors l, l+lanes, ... of the zero-padded row
+    (zipped with x) in order, adds its vector lanes, then ``block_tree``."""
+    chunk = lanes * vw
+    Np = max(chunk, math.ceil(N / chunk) * chunk)
+    J = Np // chunk
+    f = fold(add, mult)
+    fr = Vect(vw, f) if vw > 1 else f
+    lane_sum = Id()
+    if vw > 1:
+        lane_sum = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
+    return C(block_tree(lanes), lane_sum, Join(), MapLocal(ReduceSeq(fr, 0)),
+             Split(J), ReorderStride(s=lanes),
+             AsVector(vw) if vw > 1 else Id(), PadTo(Np), ZipWith("x"))
+
+
+def gemv_z_variant(M: int, N: int, alpha, vw: int, lanes: int = WARP,
+                   rows_per_cta: int = 1):
+    """z = alpha * (row dots), rows grouped rows_per_cta to a CTA."""
+    assert M % rows_per_cta == 0
+    row = gemv_row_variant(N, vw, lanes)
+    return C(Map(mult_by(alpha)), Join(), Join(),
+             MapWorkgroup(Map(row)), Split(rows_per_cta))

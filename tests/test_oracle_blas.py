@@ -1,0 +1,121 @@
+"""Pins of the Fig. 5 programs: closed forms, exact rational brute force,
+and the exact-rounded sum of the standard library."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import blas
+
+
+@pytest.mark.parametrize("k", [0, 1, 5, 12, 20])
+def test_asum_closed_form(k):
+    # x_i = i/n, n = 2^k: every x_i and every partial sum is a dyadic
+    # rational with < 53 bits, so the FP64 fold is exact: sum = (n-1)/2.
+    n = 1 << k
+    x = np.arange(n) / n
+    assert blas.asum(x) == (n - 1) / 2
+    # alternating signs: abs must undo them
+    s = np.where(np.arange(n) % 2 == 1, -x, x)
+    assert blas.asum(s) == (n - 1) / 2
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1000, 1 << 16])
+def test_dot_closed_forms(n):
+    assert blas.dot(np.full(n, 0.5), np.full(n, 3.0)) == 1.5 * n
+    i = np.arange(n, dtype=float)
+    assert blas.dot(i, np.ones(n)) == n * (n - 1) / 2
+    # sum i^2 = (n-1) n (2n-1) / 6
+    assert blas.dot(i, i) == (n - 1) * n * (2 * n - 1) / 6
+
+
+def test_gemv_closed_forms():
+    M, N = 37, 53
+    y = np.arange(M, dtype=float) - 10
+    # A = 1, x = 1: y' = alpha*N + beta*y
+    out = blas.gemv(np.ones((M, N)), np.ones(N), y, 2.0, 0.5)
+    assert np.array_equal(out, 2.0 * N + 0.5 * y)
+    # A_ij = i (row index), x_j = j: y'_i = alpha * i * N(N-1)/2 + beta*y_i;
+    # a transposed A would give alpha * sum_j j*j instead.
+    A = np.repeat(np.arange(M, dtype=float)[:, None], N, axis=1)
+    x = np.arange(N, dtype=float)
+    out = blas.gemv(A, x, y, 1.0, 0.5)
+    assert np.array_equal(out, np.arange(M) * (N * (N - 1) / 2) + 0.5 * y)
+    # A_ij = j: every row equals sum_j j * x_j
+    A2 = np.repeat(np.arange(N, dtype=float)[None, :], M, axis=0)
+    out = blas.gemv(A2, np.ones(N), y, 1.0, 0.0)
+    assert np.array_equal(out, np.full(M, N * (N - 1) / 2))
+
+
+def test_gemv_beta_zero_does_not_read_y():
+    out = blas.gemv(np.ones((3, 4)), np.ones(4), np.full(3, np.nan), 1.0, 0.0)
+    assert np.array_equal(out, np.full(3, 4.0))
+    # beta != 0 reads y, and NaN propagates
+    out = blas.gemv(np.ones((3, 4)), np.ones(4), np.full(3, np.nan), 1.0, 1.0)
+    assert np.isnan(out).all()
+
+
+def test_empty_inputs():
+    assert blas.asum(np.zeros(0)) == 0.0
+    assert blas.dot(np.zeros(0), np.zeros(0)) == 0.0
+    assert blas.gemv(np.zeros((0, 3)), np.ones(3), np.zeros(0), 1.0, 1.0).size == 0
+    out = blas.gemv(np.zeros((3, 0)), np.zeros(0), np.array([1.0, 2.0, 3.0]), 1.0, 0.5)
+    assert out.tolist() == [0.5, 1.0, 1.5]
+
+
+def _dyadic(rng, shape, bits=8):
+    return rng.integers(-(1 << bits), 1 << bits, shape) / 16.0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_brute_force_fractions(seed):
+    """Tiny dyadic inputs: every FP64 operation is exact, so the oracle
+    must equal the exact rational value computed with Fraction."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 17))
+    x, y = _dyadic(rng, n), _dyadic(rng, n)
+    assert blas.asum(x) == float(sum(abs(Fraction(v)) for v in x))
+    assert blas.dot(x, y) == float(sum(Fraction(a) * Fraction(b) for a, b in zip(x, y)))
+    a = 1.5
+    assert blas.scal(a, x).tolist() == [float(Fraction(a) * Fraction(v)) for v in x]
+    M = int(rng.integers(1, 6))
+    A = _dyadic(rng, (M, n))
+    yy = _dyadic(rng, M)
+    out = blas.gemv(A, x, yy, 2.0, -0.5)
+    exp = [float(Fraction(2) * sum(Fraction(A[i, j]) * Fraction(x[j]) for j in range(n))
+                 + Fraction(-1, 2) * Fraction(yy[i])) for i in range(M)]
+    assert out.tolist() == exp
+
+
+@pytest.mark.parametrize("n", [10, 4097, 1 << 18])
+def test_fold_within_fp64_bound_of_exact_sum(n):
+    # math.fsum is the correctly rounded sum; a left fold in FP64 is within
+    # (n-1) * 2^-53 * sum|t| of the exact value.
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n)
+    y = rng.standard_normal(n)
+    exact = math.fsum(np.abs(x))
+    assert abs(blas.asum(x) - exact) <= n * 2 ** -53 * exact
+    prods = x * y            # exact products would need 106 bits; bound both
+    ex = math.fsum(prods)
+    terms = math.fsum(np.abs(prods))
+    assert abs(blas.dot(x, y) - ex) <= (n + 1) * 2 ** -53 * terms
+
+
+def test_scal_fp32_product_is_correctly_rounded():
+    # the FP64 product of two fp32 values is exact (48 significant bits), so
+    # rounding it once to fp32 is the correctly rounded fp32 product.
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(1000).astype(np.float32)
+    out = blas.scal(1.5, x)
+    for v, o in zip(x[:50], out[:50]):
+        assert Fraction(float(v)) * Fraction(3, 2) == Fraction(float(o))
+
+
+def test_tolerance_formula():
+    u = 2.0 ** -24
+    assert blas.tolerance(1 << 20, 10.0) == 4 * u * 20 * 10.0
+    assert blas.tolerance(1, 3.0) == 4 * u * 1 * 3.0
+    assert blas.tolerance(3, 1.0) == 4 * u * 2
+    assert blas.tolerance(1000, 1.0) == 4 * u * 10
