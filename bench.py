@@ -1,0 +1,413 @@
+"""Benchmark of the liftblas hot path on GB300.
+
+Default workload (the dot/scal configuration): fp32 vectors x, y of
+n = 2^26 elements ~ N(0,1) (seed 1), alpha = 1.5.  One step is
+dot(x, y) followed by scal(alpha, x) -> z, each through the C-ABI with the
+policy-picked variant.  The metric is HBM GB/s of algorithmic traffic
+(dot reads 8n bytes, scal reads 4n and writes 4n bytes; 16n per step) and
+its fraction of the measured HBM peak.  Inputs (3 x 256 MiB) exceed the
+129 MB L2, so no flush is needed between steps.
+
+Other workloads (``--workload``): asum (n = 2^20, L2 flushed before every
+step), gemv_square (8192 x 8192), gemv_tall (65536 x 1024).
+
+Under torchrun each rank runs its own replica on its own GPU (the ops of
+one step do not exchange data); value is the bytes of all ranks divided by
+the slowest rank's time.
+
+``--impl reference`` times the CPU oracle instead (the FP64 pattern
+interpreter on the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "dot_scal": dict(n=1 << 26, desc="dot(x,y) + scal(1.5,x) fp32, n=2^26, N(0,1) seed 1"),
+    "asum": dict(n=1 << 20, desc="asum(x) fp32, n=2^20, U(-1,1) seed 0, L2 flushed per step"),
+    "gemv_square": dict(M=8192, N=8192, desc="gemv fp32 8192x8192, alpha=1, beta=0.5, seed 2"),
+    "gemv_tall": dict(M=65536, N=1024, desc="gemv fp32 65536x1024, alpha=1, beta=0.5, seed 2"),
+}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1502_02389_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources ('tag hash bytes' lines)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = csrc_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) == 3 and f[0] == kernel_tag and f[1] == want:
+            return float(f[2])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_1502_02389_gb300 import build, lift, synth
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    build.build()
+    lift.lift_init(local)
+    dev = torch.device("cuda", local)
+    wl = args.workload
+    s = torch.cuda.current_stream()
+    launches_per_step = 0
+    kernels = []   # (tag, bytes per launch, start events, end events)
+
+    if wl == "dot_scal":
+        n = WORKLOADS[wl]["n"]
+        xh, yh, alpha = synth.dot_scal(n)
+        x, y = torch.from_numpy(xh).to(dev), torch.from_numpy(yh).to(dev)
+        z = torch.empty_like(x)
+        r = torch.zeros(1, device=dev)
+        vd = lift.lift_pick(lift.OP_DOT, n)
+        vs = lift.lift_pick(lift.OP_SCAL, n)
+        pd = lift.lift_variant_describe(lift.OP_DOT, vd)
+        ps = lift.lift_variant_describe(lift.OP_SCAL, vs)
+        launches_per_step = pd["passes"] + 1
+        bytes_step = 16 * n
+        kdot = ["dot:" + pd["name"], 8 * n, [], []]
+        kscal = ["scal:" + ps["name"], 8 * n, [], []]
+        kernels = [kdot, kscal]
+
+        def step(timed):
+            if timed:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(s)
+            lift.lift_dot_v(vd, x, y, n, r)
+            if timed:
+                ev2 = torch.cuda.Event(enable_timing=True)
+                ev[1].record(s)
+                kdot[2].append(ev[0]); kdot[3].append(ev[1])
+                ev2.record(s)
+            lift.lift_scal_v(vs, n, float(alpha), x, z)
+            if timed:
+                ev3 = torch.cuda.Event(enable_timing=True)
+                ev3.record(s)
+                kscal[2].append(ev2); kscal[3].append(ev3)
+
+        def e2e_step(xp, yp, zp, rp):
+            x.copy_(xp, non_blocking=True)
+            y.copy_(yp, non_blocking=True)
+            lift.lift_dot_v(vd, x, y, n, r)
+            lift.lift_scal_v(vs, n, float(alpha), x, z)
+            rp.copy_(r, non_blocking=True)
+            zp.copy_(z, non_blocking=True)
+
+        host = dict(xp=torch.from_numpy(xh).pin_memory(), yp=torch.from_numpy(yh).pin_memory(),
+                    zp=torch.empty(n, dtype=torch.float32).pin_memory(),
+                    rp=torch.empty(1, dtype=torch.float32).pin_memory())
+        h2d, d2h = 8 * n, 4 * n + 4
+        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pd["name"], ps["name"]],
+                  "l2": "no flush: inputs 3 x 256 MiB exceed the 129 MB L2"}
+    elif wl == "asum":
+        n = WORKLOADS[wl]["n"]
+        xh = synth.asum_small(n)
+        x = torch.from_numpy(xh).to(dev)
+        r = torch.zeros(1, device=dev)
+        flush = torch.ones(128 << 20, dtype=torch.float32, device=dev)
+        va = lift.lift_pick(lift.OP_ASUM, n)
+        pa = lift.lift_variant_describe(lift.OP_ASUM, va)
+        launches_per_step = pa["passes"]
+        bytes_step = 4 * n
+        kas = ["asum:" + pa["name"], 4 * n, [], []]
+        kernels = [kas]
+
+        def step(timed):
+            flush.sum()     # read 512 MiB: evicts x from L2 and leaves no dirty lines
+            if timed:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(s)
+            lift.lift_asum_v(va, x, n, r)
+            if timed:
+                ev[1].record(s)
+                kas[2].append(ev[0]); kas[3].append(ev[1])
+
+        def e2e_step(xp, rp):
+            x.copy_(xp, non_blocking=True)
+            lift.lift_asum_v(va, x, n, r)
+            rp.copy_(r, non_blocking=True)
+
+        host = dict(xp=torch.from_numpy(xh).pin_memory(), rp=torch.empty(1).pin_memory())
+        h2d, d2h = 4 * n, 4
+        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
+                  "l2": "flushed before every step (a 512 MiB read, outside the kernel events)"}
+    else:
+        M, N = WORKLOADS[wl]["M"], WORKLOADS[wl]["N"]
+        Ah, xh, yh, a, b = synth.gemv(M, N)
+        A, xv, y0 = (torch.from_numpy(t).to(dev) for t in (Ah, xh, yh))
+        yv = y0.clone()
+        vg = lift.lift_pick(lift.OP_GEMV, M * N, M, N)
+        pg = lift.lift_variant_describe(lift.OP_GEMV, vg)
+        launches_per_step = 1
+        bytes_step = 4 * M * N + 4 * N + 8 * M
+        kg = ["gemv:" + pg["name"], bytes_step, [], []]
+        kernels = [kg]
+
+        def step(timed):
+            if timed:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(s)
+            lift.lift_gemv_v(vg, M, N, float(a), A, N, xv, float(b), yv)
+            if timed:
+                ev[1].record(s)
+                kg[2].append(ev[0]); kg[3].append(ev[1])
+
+        def e2e_step(Ap, xp, yp, outp):
+            A.copy_(Ap, non_blocking=True)
+            xv.copy_(xp, non_blocking=True)
+            yv.copy_(yp, non_blocking=True)
+            lift.lift_gemv_v(vg, M, N, float(a), A, N, xv, float(b), yv)
+            outp.copy_(yv, non_blocking=True)
+
+        host = dict(Ap=torch.from_numpy(Ah).pin_memory(), xp=torch.from_numpy(xh).pin_memory(),
+                    yp=torch.from_numpy(yh).pin_memory(), outp=torch.empty(M).pin_memory())
+        h2d, d2h = 4 * M * N + 4 * N + 4 * M, 4 * M
+        config = {"workload": WORKLOADS[wl]["desc"], "M": M, "N": N, "variants": [pg["name"]],
+                  "l2": "no flush: A is 256 MiB, larger than the 129 MB L2"}
+
+    # ---- warm-up, then K timed steps bracketed by barrier + synchronize
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(s)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * bytes_step * args.steps / (ms / 1e3) / 1e9
+
+    # ---- per-kernel durations (events on the launching stream)
+    per_kernel = {}
+    for tag, kb, starts, ends in kernels:
+        d = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        avg = sum(d) / len(d)
+        per_kernel[tag] = {"ms": avg, "gbs": kb / (avg / 1e3) / 1e9, "bytes": kb}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    peak, src = peaks()
+    tr = traffic_for(dom.split(":", 1)[1])
+    roof = {"bound": "hbm", "achieved": round(per_kernel[dom]["gbs"], 1), "peak": peak,
+            "unit": "GB/s", "frac": round(per_kernel[dom]["gbs"] / peak, 4),
+            "traffic": tr, "kernel": dom, "peak_source": f"{src} hbm_gbs (copy bandwidth)",
+            "algorithmic_bytes_per_launch": kernels[[k[0] for k in kernels].index(dom)][1]}
+
+    # ---- end to end through the C-ABI with host buffers
+    for _ in range(2):
+        e2e_step(**host)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ek = max(3, min(args.steps, 10))
+    e0.record(s)
+    for _ in range(ek):
+        e2e_step(**host)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1) / ek
+    if dist:
+        t = torch.tensor([ems], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
+    assert lift.lift_read_status() == 0
+    return dict(value=value, ms_step=ms_step, roofline=roof, per_kernel=per_kernel, clocks=clk,
+                e2e=e2e, config=config, launches=launches_per_step * args.steps, peak=peak)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(workload: str, budget_s: float):
+    """Time the oracle, as it stands, on the workload (or a bounded slice of
+    it) until about ``budget_s`` seconds of CPU work; returns GB/s of
+    algorithmic bytes and a description of the sample."""
+    import numpy as np
+
+    from oracle import blas
+    from paper_1502_02389_gb300 import synth
+
+    if workload == "dot_scal":
+        n = WORKLOADS[workload]["n"]
+        x, y, alpha = synth.dot_scal(n)
+        work = lambda: (blas.dot(x, y), blas.scal(float(alpha), x))  # noqa: E731
+        bytes_one, what = 16 * n, f"full step (dot + scal, n=2^26)"
+    elif workload == "asum":
+        n = WORKLOADS[workload]["n"]
+        x = synth.asum_small(n)
+        work = lambda: blas.asum(x)  # noqa: E731
+        bytes_one, what = 4 * n, "full step (asum, n=2^20)"
+    else:
+        M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
+        A, xv, yv, a, b = synth.gemv(M, N)
+        rows = max(1, M // 16)
+        As, ys = A[:rows], yv[:rows]
+        work = lambda: blas.gemv(As, xv, ys, float(a), float(b))  # noqa: E731
+        bytes_one, what = 4 * rows * N + 4 * N + 8 * rows, f"first {rows} of {M} rows"
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        work()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el >= 30.0:
+            break
+    return bytes_one * reps / el / 1e9, f"{what}, {reps} repetition(s) in {el:.1f} s", el / reps
+
+
+def run_reference(args):
+    val, sample, sec = oracle_sample(args.workload, budget_s=max(3.0, 20.0 / max(1, args.steps)))
+    out = {"metric": METRIC, "value": round(val, 4), "unit": "GB/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOADS[args.workload]["desc"]},
+           "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+METRIC = "HBM GB/s (frac of peak) for asum/dot/gemv; learned vs autotuned variant gap"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dot_scal", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, dist)
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            val, sample, _ = oracle_sample(args.workload, budget_s=10.0)
+            cpu = {"value": round(val, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": sample}
+        out = {"metric": METRIC, "value": round(res["value"], 2), "unit": "GB/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(res["ms_step"], 5), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": res["config"],
+               "frac_of_peak": round(res["value"] / world / res["peak"], 4),
+               "roofline": res["roofline"],
+               "kernels": {k: {"ms": round(v["ms"], 5), "gbs": round(v["gbs"], 1)}
+                           for k, v in res["per_kernel"].items()},
+               "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+               "gpu_launches": res["launches"]}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * liftblas -- C-ABI of the GB300 (sm_103a) kernels for the fused map/reduce
+ * programs of Steuwer, Fensch and Dubach, "Patterns and Rewrite Rules for
+ * Systematic Code Generation" (arXiv 1502.02389):
+ *
+ *   scal(a, x)          = map(mult(a), x)                          Fig. 5
+ *   asum(x)             = reduce(add, 0) . map(abs, x)             Fig. 5
+ *   dot(x, y)           = reduce(add, 0) . map(mult) . zip(x, y)   Fig. 5
+ *   gemv(A, x, y, a, b) = y <- a*A*x + b*y, map(dot) over rows     Fig. 5, Sec. 5.1
+ *
+ * Each kernel variant is one low-level expression derived from these with
+ * the rewrite rules of Fig. 3 and Fig. 4; its integer parameters (split
+ * tile, vector width, reorder-stride, tree depth, combine passes, staging)
+ * are compile-time template parameters.  lift_variant_describe lists them.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers, owned by the caller; the
+ *    library never frees or keeps them.  Arrays are contiguous (no BLAS inc
+ *    strides); gemv's A is row-major with leading dimension lda >= N.
+ *  - Sizes are int64_t element counts.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call is asynchronous on that stream: the status
+ *    returned reports argument validation and launch errors only.
+ *  - Nothing aborts or throws across the ABI.  Invalid arguments return
+ *    LIFT_ERR_INVALID_ARG before any launch: n < 0, M < 0, N < 0, lda < N,
+ *    or a NULL pointer for an array that would be read or written.
+ *  - n == 0 is valid: a reduction writes 0; gemv with N == 0 computes
+ *    y <- b*y, and with M == 0 does nothing.
+ *  - A pointer that is not aligned for a variant's vector width or for
+ *    TMA bulk copies (16 B) makes the library use the same variant family's
+ *    guarded scalar-load form instead; it is not an error.
+ *  - The reductions use a per-device workspace allocated by lift_init
+ *    (partials, a ticket counter, a status word).  Reductions that run at
+ *    the same time on different streams of one device share it and race:
+ *    order them on one stream.
+ *  - lift_last_error() returns a detail message for the last failure of the
+ *    calling thread.
+ */
+#ifndef LIFT_H
+#define LIFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LIFT_OK = 0,
+  LIFT_ERR_INVALID_ARG = 1,
+  LIFT_ERR_UNSUPPORTED = 2,
+  LIFT_ERR_CUDA = 3,
+  LIFT_ERR_NO_MEMORY = 4,
+  LIFT_ERR_TIMEOUT = 5,
+  LIFT_ERR_NOT_INITIALIZED = 6
+} lift_status;
+
+typedef enum { LIFT_F32 = 0, LIFT_BF16 = 1, LIFT_FP8_E4M3 = 2 } lift_dtype;
+
+/* Operation ids: the four Fig. 5 programs, then the mixed-precision
+ * reductions (stored bf16 or fp8-e4m3 inputs). */
+typedef enum {
+  LIFT_OP_ASUM = 0,
+  LIFT_OP_DOT = 1,
+  LIFT_OP_SCAL = 2,
+  LIFT_OP_GEMV = 3,
+  LIFT_OP_ASUM_BF16 = 4,
+  LIFT_OP_DOT_BF16 = 5,
+  LIFT_OP_ASUM_FP8 = 6,
+  LIFT_OP_DOT_FP8 = 7,
+  LIFT_NUM_OPS = 8
+} lift_op;
+
+/* ------------------------------------------------------------------------
+ * Library state
+ * ------------------------------------------------------------------------ */
+
+/* Set up `device`: query its SM count and allocate the reduction workspace
+ * on it.  Must be called (once per device) before any other call on that
+ * device, outside CUDA graph capture.  Calling it again is a no-op.
+ * Returns LIFT_ERR_CUDA / LIFT_ERR_NO_MEMORY on failure. */
+lift_status lift_init(int device);
+
+/* Free the workspaces of every initialised device.  Synchronises them. */
+lift_status lift_finalize(void);
+
+const char* lift_status_string(lift_status s);
+const char* lift_last_error(void);
+
+/* Number of SMs of the current device (0 if not initialised). */
+int lift_sm_count(void);
+
+/* Read (and, if `clear`, reset) the current device's status word, where
+ * kernels record a device-side wait that gave up (LIFT_ERR_TIMEOUT).
+ * Synchronises with the device.  Returns 0, a lift_status code, or
+ * LIFT_ERR_NOT_INITIALIZED / LIFT_ERR_CUDA for the read itself. */
+int lift_read_status(int clear);
+
+/* ------------------------------------------------------------------------
+ * fp32 programs (Fig. 5).  The policy picks the variant (see
+ * lift_set_policy).
+ * ------------------------------------------------------------------------ */
+
+/* asum: *result = sum_i |x_i| (Fig. 5: reduce(add,0) . map(abs)).
+ * x: n floats; result: one float (device).  Accumulates in fp32 per
+ * thread and combines the per-CTA partials in FP64. */
+lift_status lift_asum(const float* x, int64_t n, float* result, void* stream);
+
+/* dot: *result = sum_i x_i * y_i (Fig. 5: reduce(add,0) . map(mult) . zip). */
+lift_status lift_dot(const float* x, const float* y, int64_t n, float* result, void* stream);
+
+/* scal: y_i = alpha * x_i, one correctly rounded fp32 multiply per element
+ * (Fig. 5 and Fig. 2: map(mult(alpha))).  y == x (in place) is allowed;
+ * other overlaps are not. */
+lift_status lift_scal(int64_t n, float alpha, const float* x, float* y, void* stream);
+
+/* gemv: y_i <- alpha * sum_j A[i*lda + j] * x_j + beta * y_i, i < M, j < N
+ * (Fig. 5, "as defined by the BLAS library", Sec. 5.1).  A row-major M x N
+ * with lda >= N; x: N floats; y: M floats, read only when beta != 0.
+ * Per row: z = fl(alpha * dot); y = fl(z + fl(beta * y)). */
+lift_status lift_gemv(int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
+                      const float* x, float beta, float* y, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Explicit variants (the autotuner's interface).  `variant` indexes the
+ * op's variant list (0 .. lift_variant_count(op)-1); -1 means "ask the
+ * policy".  result_f64 (optional, may be NULL) receives the FP64 value of
+ * the final combine before its rounding to fp32.
+ * ------------------------------------------------------------------------ */
+lift_status lift_asum_v(int variant, const float* x, int64_t n, float* result,
+                        double* result_f64, void* stream);
+lift_status lift_dot_v(int variant, const float* x, const float* y, int64_t n,
+                       float* result, double* result_f64, void* stream);
+lift_status lift_scal_v(int variant, int64_t n, float alpha, const float* x, float* y,
+                        void* stream);
+lift_status lift_gemv_v(int variant, int64_t M, int64_t N, float alpha, const float* A,
+                        int64_t lda, const float* x, float beta, float* y, void* stream);
+
+/* Rewrite parameters of one variant.
+ *  tile     split^tile: elements a CTA takes per pipeline step (gemv: 0)
+ *  vw       asVector^vw: elements per load (1, 4 = 128-bit, 8 = 256-bit)
+ *  threads  local threads per CTA (map-local width)
+ *  stride   1: reorder-stride (thread t reads vector t + threads*j);
+ *           0: contiguous chunk per thread
+ *  tree     in-CTA iterate depth: 0 warp shuffles only, 1 + shared memory,
+ *           2 + cluster distributed shared memory
+ *  cluster  CTAs per cluster (1 = none)
+ *  passes   1: last-CTA combine in the same launch; 2: second kernel
+ *  stages   0: direct vector loads; k >= 2: k-deep TMA bulk-copy ring
+ *  rows     gemv: rows per warp-group step (0 otherwise)
+ *  lanes    gemv: threads that share one row (0 otherwise)
+ *  final_threads  threads of the FP64 final combine
+ */
+typedef struct {
+  int op, id, tile, vw, threads, stride, tree, cluster, passes, stages, rows, lanes,
+      final_threads;
+  char name[64];
+} lift_variant_info;
+
+int lift_variant_count(int op);
+lift_status lift_variant_describe(int op, int id, lift_variant_info* out);
+
+/* CTAs a variant launches for a problem of n elements (gemv: n = M) on
+ * the current device -- the map-workgroup width of its expression. */
+lift_status lift_variant_grid(int op, int id, int64_t n, int64_t* grid);
+
+/* ------------------------------------------------------------------------
+ * Mixed precision (stored bf16, or fp8-e4m3 with one fp32 scale per 4096
+ * consecutive elements; the last block may be shorter).
+ *   bf16: x is n uint16 bit patterns; xscale must be NULL.
+ *   fp8:  x is n uint8 E4M3 bit patterns; xscale holds ceil(n/4096) floats;
+ *         element i stands for q_i * xscale[i / 4096].
+ * Per-thread fp32 Kahan-compensated sums of the exactly widened values
+ * (bf16 -> fp32 is exact; an fp8 product is exact in fp32), one scale
+ * multiply per block, FP64 combine across CTAs.  result: one float;
+ * result_f64 (optional): the FP64 combine before rounding.
+ * ------------------------------------------------------------------------ */
+lift_status lift_asum_ex(lift_dtype t, const void* x, const float* xscale, int64_t n,
+                         float* result, double* result_f64, void* stream);
+lift_status lift_dot_ex(lift_dtype t, const void* x, const float* xscale, const void* y,
+                        const float* yscale, int64_t n, float* result, double* result_f64,
+                        void* stream);
+lift_status lift_asum_ex_v(int variant, lift_dtype t, const void* x, const float* xscale,
+                           int64_t n, float* result, double* result_f64, void* stream);
+lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float* xscale,
+                          const void* y, const float* yscale, int64_t n, float* result,
+                          double* result_f64, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Variant policy.
+ *   LIFT_POLICY_FIXED: the per-op default variant (or lift_set_variant's).
+ *   LIFT_POLICY_TABLE: a tuned table (path: a text file written by the
+ *                      autotuner; nearest shape in log2 size).
+ *   LIFT_POLICY_MLP:   the cost model (path: weights file written by the
+ *                      trainer); argmin of the predicted times.
+ * ------------------------------------------------------------------------ */
+typedef enum { LIFT_POLICY_FIXED = 0, LIFT_POLICY_TABLE = 1, LIFT_POLICY_MLP = 2 } lift_policy;
+
+lift_status lift_set_policy(int policy, const char* path);
+/* Force `variant` for `op` (-1 clears the override). */
+lift_status lift_set_variant(int op, int variant);
+/* The variant the current policy would use. M, N: gemv shape (else 0). */
+lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
+
+/* The 10 cost-model features of a call, written to out[0..9]: one-hot op
+ * family (asum, dot, scal, gemv), log2(n+1)/32, log2(M+1)/16,
+ * log2(N+1)/16, one-hot element type (fp32, bf16, fp8).  For gemv the
+ * size feature uses n = M*N.  Host-only; needs no device. */
+lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIFT_H */

@@ -1,0 +1,586 @@
+// C-ABI of liftblas (include/lift.h): device state, argument validation,
+// variant registry and policy, and the extern "C" entry points.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+#include "lift_internal.cuh"
+
+namespace lift {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+lift_status set_error(lift_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+lift_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LIFT_OK;
+  return set_error(e == cudaErrorMemoryAllocation ? LIFT_ERR_NO_MEMORY : LIFT_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// device state
+// ---------------------------------------------------------------------------
+static std::mutex g_mu;
+static std::map<int, DeviceState*> g_states;
+constexpr int64_t kPartialCapacity = 1 << 14;
+
+DeviceState* current_state() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_states.find(dev);
+  return it == g_states.end() ? nullptr : it->second;
+}
+
+static lift_status init_device(int device) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_states.count(device)) return LIFT_OK;
+  }
+  int prev = -1;
+  lift_status rc = cuda_check(cudaGetDevice(&prev), "cudaGetDevice");
+  if (rc != LIFT_OK) return rc;
+  rc = cuda_check(cudaSetDevice(device), "cudaSetDevice");
+  if (rc != LIFT_OK) return rc;
+  DeviceState* st = new DeviceState();
+  st->device = device;
+  rc = cuda_check(cudaDeviceGetAttribute(&st->sm_count, cudaDevAttrMultiProcessorCount, device),
+                  "SM count");
+  if (rc == LIFT_OK)
+    rc = cuda_check(cudaMalloc(&st->ws.partials, kPartialCapacity * sizeof(float)), "workspace");
+  if (rc == LIFT_OK)
+    rc = cuda_check(cudaMalloc(&st->ws.partials64, 2 * kPartialCapacity * sizeof(double)),
+                    "workspace");
+  if (rc == LIFT_OK) rc = cuda_check(cudaMalloc(&st->ws.tickets, 64 * sizeof(unsigned)), "workspace");
+  if (rc == LIFT_OK) rc = cuda_check(cudaMalloc(&st->ws.status, sizeof(int)), "workspace");
+  if (rc == LIFT_OK) rc = cuda_check(cudaMemset(st->ws.tickets, 0, 64 * sizeof(unsigned)), "memset");
+  if (rc == LIFT_OK) rc = cuda_check(cudaMemset(st->ws.status, 0, sizeof(int)), "memset");
+  if (rc == LIFT_OK) rc = cuda_check(cudaDeviceSynchronize(), "init sync");
+  st->ws.capacity = kPartialCapacity;
+  if (rc != LIFT_OK) {
+    cudaFree(st->ws.partials);
+    cudaFree(st->ws.partials64);
+    cudaFree(st->ws.tickets);
+    cudaFree(st->ws.status);
+    delete st;
+    cudaSetDevice(prev);
+    return rc;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_states[device] = st;
+  }
+  cudaSetDevice(prev);
+  return LIFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// registry
+// ---------------------------------------------------------------------------
+static std::vector<Variant> g_ops[LIFT_NUM_OPS];
+static std::once_flag g_reg_once;
+
+static void build_registry() {
+  register_reduce_f32(g_ops[LIFT_OP_ASUM], g_ops[LIFT_OP_DOT]);
+  register_scal(g_ops[LIFT_OP_SCAL]);
+  register_gemv(g_ops[LIFT_OP_GEMV]);
+  register_mixed(g_ops);
+}
+
+std::vector<Variant>& registry(int op) {
+  std::call_once(g_reg_once, build_registry);
+  return g_ops[op];
+}
+
+int64_t persistent_grid(const void* kernel, int threads, size_t smem, int cluster) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int64_t> cache;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({dev, kernel});
+    if (it != cache.end()) return it->second;
+  }
+  DeviceState* st = current_state();
+  if (!st) return 0;
+  if (smem > 0 &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+    return 0;
+  int64_t g = (int64_t)per_sm * st->sm_count;
+  g = g / cluster * cluster;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[{dev, kernel}] = g;
+  return g;
+}
+
+lift_status launch_config(const void* kernel, dim3 grid, dim3 block, size_t smem, int cluster,
+                          cudaStream_t s, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (cluster > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cuda_check(cudaLaunchKernelExC(&cfg, kernel, args), "kernel launch");
+}
+
+// ---------------------------------------------------------------------------
+// policy
+// ---------------------------------------------------------------------------
+struct TableEntry {
+  double ln, lm, lN;
+  int variant;
+};
+
+struct Mlp {
+  int d_in = 0, h1 = 0, h2 = 0, V = 0;
+  int offsets[LIFT_NUM_OPS] = {0};
+  std::vector<float> W1, b1, W2, b2, W3, b3;
+};
+
+static int g_policy = LIFT_POLICY_FIXED;
+static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1};
+static std::vector<TableEntry> g_table[LIFT_NUM_OPS];
+static Mlp g_mlp;
+static std::mutex g_policy_mu;
+
+// Defaults of the FIXED policy (variant names; looked up at first use).
+static const char* kDefaultName[LIFT_NUM_OPS] = {
+    "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t4096_v4_ldg", "gemv_w8_v4_u4",
+    nullptr, nullptr, nullptr, nullptr};
+
+static int find_variant(int op, const char* name) {
+  auto& L = registry(op);
+  if (name)
+    for (size_t i = 0; i < L.size(); ++i)
+      if (strcmp(L[i].info.name, name) == 0) return (int)i;
+  return L.empty() ? -1 : 0;
+}
+
+}  // namespace lift
+
+using namespace lift;
+
+extern "C" {
+
+// Features of a call for the cost model: one-hot op family (asum, dot,
+// scal, gemv), log2(n+1)/32, log2(M+1)/16, log2(N+1)/16, one-hot dtype
+// (fp32, bf16, fp8).  For gemv n = M*N.
+lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out) {
+  if (op < 0 || op >= LIFT_NUM_OPS || !out) return LIFT_ERR_INVALID_ARG;
+  static const int fam[LIFT_NUM_OPS] = {0, 1, 2, 3, 0, 1, 0, 1};
+  static const int dt[LIFT_NUM_OPS] = {0, 0, 0, 0, 1, 1, 2, 2};
+  for (int i = 0; i < 10; ++i) out[i] = 0.f;
+  out[fam[op]] = 1.f;
+  if (op == LIFT_OP_GEMV) n = M * N;
+  out[4] = (float)(log2((double)n + 1.0) / 32.0);
+  out[5] = (float)(log2((double)M + 1.0) / 16.0);
+  out[6] = (float)(log2((double)N + 1.0) / 16.0);
+  out[7 + dt[op]] = 1.f;
+  return LIFT_OK;
+}
+
+}  // extern "C"
+
+namespace lift {
+
+static int mlp_pick(int op, int64_t n, int64_t M, int64_t N) {
+  const Mlp& m = g_mlp;
+  float f[10];
+  lift_features(op, n, M, N, f);
+  std::vector<float> h1(m.h1), h2(m.h2);
+  for (int j = 0; j < m.h1; ++j) {
+    float s = m.b1[j];
+    for (int i = 0; i < m.d_in; ++i) s += f[i] * m.W1[i * m.h1 + j];
+    h1[j] = s > 0.f ? s : 0.f;
+  }
+  for (int j = 0; j < m.h2; ++j) {
+    float s = m.b2[j];
+    for (int i = 0; i < m.h1; ++i) s += h1[i] * m.W2[i * m.h2 + j];
+    h2[j] = s > 0.f ? s : 0.f;
+  }
+  const int cnt = (int)registry(op).size();
+  int best = 0;
+  float best_t = INFINITY;
+  for (int v = 0; v < cnt; ++v) {
+    const int o = m.offsets[op] + v;
+    if (o >= m.V) break;
+    float s = m.b3[o];
+    for (int i = 0; i < m.h2; ++i) s += h2[i] * m.W3[i * m.V + o];
+    if (s < best_t) {
+      best_t = s;
+      best = v;
+    }
+  }
+  return best;
+}
+
+static int table_pick(int op, int64_t n, int64_t M, int64_t N) {
+  const auto& T = g_table[op];
+  if (T.empty()) return -1;
+  const double ln = log2((double)(op == LIFT_OP_GEMV ? M * N : n) + 1.0);
+  const double lm = log2((double)M + 1.0), lN = log2((double)N + 1.0);
+  double best = INFINITY;
+  int v = -1;
+  for (const auto& e : T) {
+    const double d = (e.ln - ln) * (e.ln - ln) + (e.lm - lm) * (e.lm - lm) + (e.lN - lN) * (e.lN - lN);
+    if (d < best) {
+      best = d;
+      v = e.variant;
+    }
+  }
+  return v;
+}
+
+static int pick_variant(int op, int64_t n, int64_t M, int64_t N) {
+  std::lock_guard<std::mutex> lk(g_policy_mu);
+  if (g_override[op] >= 0) return g_override[op];
+  int v = -1;
+  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0) v = mlp_pick(op, n, M, N);
+  if (g_policy == LIFT_POLICY_TABLE) v = table_pick(op, n, M, N);
+  if (v < 0) v = find_variant(op, kDefaultName[op]);
+  return v;
+}
+
+static bool ptr_ok(const void* p, int bytes) { return p == nullptr || aligned(p, bytes); }
+
+// Resolve the variant to run: explicit id or policy pick, then the guarded
+// form when a pointer is not aligned for the chosen variant.
+static lift_status resolve(int op, int variant, const Args& a, const Variant** out) {
+  auto& L = registry(op);
+  if (L.empty()) return set_error(LIFT_ERR_UNSUPPORTED, "no variants for op");
+  if (variant < -1 || variant >= (int)L.size())
+    return set_error(LIFT_ERR_INVALID_ARG, "variant id out of range");
+  if (variant < 0) variant = pick_variant(op, a.n, a.M, a.N);
+  const Variant* v = &L[variant];
+  const int al = v->align_bytes;
+  bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
+  if (op == LIFT_OP_GEMV) ok = ok && ((a.lda * 4) % al == 0);
+  if (!ok && v->fallback >= 0) v = &L[v->fallback];
+  *out = v;
+  return LIFT_OK;
+}
+
+static lift_status run(int op, int variant, const Args& a, void* stream) {
+  DeviceState* st = current_state();
+  if (!st) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  const Variant* v = nullptr;
+  lift_status rc = resolve(op, variant, a, &v);
+  if (rc != LIFT_OK) return rc;
+  return v->launch(*v, a, static_cast<cudaStream_t>(stream));
+}
+
+static bool bad_n(int64_t n) { return n < 0; }
+
+}  // namespace lift
+
+extern "C" {
+
+lift_status lift_init(int device) { return init_device(device); }
+
+lift_status lift_finalize(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  for (auto& kv : g_states) {
+    cudaSetDevice(kv.first);
+    cudaDeviceSynchronize();
+    cudaFree(kv.second->ws.partials);
+    cudaFree(kv.second->ws.partials64);
+    cudaFree(kv.second->ws.tickets);
+    cudaFree(kv.second->ws.status);
+    delete kv.second;
+  }
+  g_states.clear();
+  if (prev >= 0) cudaSetDevice(prev);
+  return LIFT_OK;
+}
+
+const char* lift_status_string(lift_status s) {
+  switch (s) {
+    case LIFT_OK: return "ok";
+    case LIFT_ERR_INVALID_ARG: return "invalid argument";
+    case LIFT_ERR_UNSUPPORTED: return "unsupported";
+    case LIFT_ERR_CUDA: return "CUDA error";
+    case LIFT_ERR_NO_MEMORY: return "out of device memory";
+    case LIFT_ERR_TIMEOUT: return "device wait timed out";
+    case LIFT_ERR_NOT_INITIALIZED: return "not initialised";
+  }
+  return "unknown status";
+}
+
+const char* lift_last_error(void) { return g_last_error.c_str(); }
+
+int lift_sm_count(void) {
+  DeviceState* st = current_state();
+  return st ? st->sm_count : 0;
+}
+
+// device status word (timeouts recorded by kernels); reading it synchronises
+int lift_read_status(int clear) {
+  DeviceState* st = current_state();
+  if (!st) return LIFT_ERR_NOT_INITIALIZED;
+  int v = 0;
+  if (cudaMemcpy(&v, st->ws.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LIFT_ERR_CUDA;
+  if (clear) cudaMemset(st->ws.status, 0, sizeof(int));
+  return v;
+}
+
+lift_status lift_asum_v(int variant, const float* x, int64_t n, float* result, double* result_f64,
+                        void* stream) {
+  if (bad_n(n) || !result || (n > 0 && !x)) return set_error(LIFT_ERR_INVALID_ARG, "asum arguments");
+  if (!aligned(x, 4)) return set_error(LIFT_ERR_INVALID_ARG, "x not 4-byte aligned");
+  Args a;
+  a.x = x;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(LIFT_OP_ASUM, variant, a, stream);
+}
+
+lift_status lift_dot_v(int variant, const float* x, const float* y, int64_t n, float* result,
+                       double* result_f64, void* stream) {
+  if (bad_n(n) || !result || (n > 0 && (!x || !y)))
+    return set_error(LIFT_ERR_INVALID_ARG, "dot arguments");
+  if (!aligned(x, 4) || !aligned(y, 4)) return set_error(LIFT_ERR_INVALID_ARG, "x/y not 4-byte aligned");
+  Args a;
+  a.x = x;
+  a.y = y;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(LIFT_OP_DOT, variant, a, stream);
+}
+
+lift_status lift_scal_v(int variant, int64_t n, float alpha, const float* x, float* y, void* stream) {
+  if (bad_n(n) || (n > 0 && (!x || !y))) return set_error(LIFT_ERR_INVALID_ARG, "scal arguments");
+  if (!aligned(x, 4) || !aligned(y, 4)) return set_error(LIFT_ERR_INVALID_ARG, "x/y not 4-byte aligned");
+  if (n > 0 && x != y) {
+    const char* xb = (const char*)x;
+    const char* yb = (const char*)y;
+    if (xb < yb + n * 4 && yb < xb + n * 4)
+      return set_error(LIFT_ERR_INVALID_ARG, "x and y overlap without being equal");
+  }
+  if (n == 0) return LIFT_OK;
+  Args a;
+  a.x = x;
+  a.out = y;
+  a.n = n;
+  a.alpha = alpha;
+  return run(LIFT_OP_SCAL, variant, a, stream);
+}
+
+lift_status lift_gemv_v(int variant, int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
+                        const float* x, float beta, float* y, void* stream) {
+  if (M < 0 || N < 0 || lda < N || lda < 0) return set_error(LIFT_ERR_INVALID_ARG, "gemv sizes");
+  if (M > 0 && !y) return set_error(LIFT_ERR_INVALID_ARG, "gemv y is NULL");
+  if (M > 0 && N > 0 && (!A || !x)) return set_error(LIFT_ERR_INVALID_ARG, "gemv A/x is NULL");
+  if (!aligned(A, 4) || !aligned(x, 4) || !aligned(y, 4))
+    return set_error(LIFT_ERR_INVALID_ARG, "gemv pointers not 4-byte aligned");
+  Args a;
+  a.A = A;
+  a.x = x;
+  a.out = y;
+  a.M = M;
+  a.N = N;
+  a.lda = lda;
+  a.n = M;
+  a.alpha = alpha;
+  a.beta = beta;
+  return run(LIFT_OP_GEMV, variant, a, stream);
+}
+
+lift_status lift_asum(const float* x, int64_t n, float* result, void* stream) {
+  return lift_asum_v(-1, x, n, result, nullptr, stream);
+}
+lift_status lift_dot(const float* x, const float* y, int64_t n, float* result, void* stream) {
+  return lift_dot_v(-1, x, y, n, result, nullptr, stream);
+}
+lift_status lift_scal(int64_t n, float alpha, const float* x, float* y, void* stream) {
+  return lift_scal_v(-1, n, alpha, x, y, stream);
+}
+lift_status lift_gemv(int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
+                      const float* x, float beta, float* y, void* stream) {
+  return lift_gemv_v(-1, M, N, alpha, A, lda, x, beta, y, stream);
+}
+
+static lift_status mixed_args(lift_dtype t, const void* x, const float* xscale, int64_t n) {
+  if (bad_n(n) || (n > 0 && !x)) return LIFT_ERR_INVALID_ARG;
+  if (t == LIFT_BF16 && xscale) return LIFT_ERR_INVALID_ARG;
+  if (t == LIFT_FP8_E4M3 && n > 0 && !xscale) return LIFT_ERR_INVALID_ARG;
+  if (t != LIFT_BF16 && t != LIFT_FP8_E4M3) return LIFT_ERR_UNSUPPORTED;
+  return LIFT_OK;
+}
+
+lift_status lift_asum_ex_v(int variant, lift_dtype t, const void* x, const float* xscale, int64_t n,
+                           float* result, double* result_f64, void* stream) {
+  if (t == LIFT_F32) return lift_asum_v(variant, (const float*)x, n, result, result_f64, stream);
+  lift_status rc = mixed_args(t, x, xscale, n);
+  if (rc != LIFT_OK || !result)
+    return set_error(rc != LIFT_OK ? rc : LIFT_ERR_INVALID_ARG, "asum_ex arguments");
+  Args a;
+  a.x = x;
+  a.xscale = xscale;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(t == LIFT_BF16 ? LIFT_OP_ASUM_BF16 : LIFT_OP_ASUM_FP8, variant, a, stream);
+}
+
+lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float* xscale, const void* y,
+                          const float* yscale, int64_t n, float* result, double* result_f64,
+                          void* stream) {
+  if (t == LIFT_F32)
+    return lift_dot_v(variant, (const float*)x, (const float*)y, n, result, result_f64, stream);
+  lift_status rc = mixed_args(t, x, xscale, n);
+  if (rc == LIFT_OK) rc = mixed_args(t, y, yscale, n);
+  if (rc != LIFT_OK || !result)
+    return set_error(rc != LIFT_OK ? rc : LIFT_ERR_INVALID_ARG, "dot_ex arguments");
+  Args a;
+  a.x = x;
+  a.y = y;
+  a.xscale = xscale;
+  a.yscale = yscale;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(t == LIFT_BF16 ? LIFT_OP_DOT_BF16 : LIFT_OP_DOT_FP8, variant, a, stream);
+}
+
+lift_status lift_asum_ex(lift_dtype t, const void* x, const float* xscale, int64_t n, float* result,
+                         double* result_f64, void* stream) {
+  return lift_asum_ex_v(-1, t, x, xscale, n, result, result_f64, stream);
+}
+lift_status lift_dot_ex(lift_dtype t, const void* x, const float* xscale, const void* y,
+                        const float* yscale, int64_t n, float* result, double* result_f64,
+                        void* stream) {
+  return lift_dot_ex_v(-1, t, x, xscale, y, yscale, n, result, result_f64, stream);
+}
+
+int lift_variant_count(int op) {
+  if (op < 0 || op >= LIFT_NUM_OPS) return 0;
+  return (int)registry(op).size();
+}
+
+lift_status lift_variant_describe(int op, int id, lift_variant_info* out) {
+  if (op < 0 || op >= LIFT_NUM_OPS || !out) return LIFT_ERR_INVALID_ARG;
+  auto& L = registry(op);
+  if (id < 0 || id >= (int)L.size()) return LIFT_ERR_INVALID_ARG;
+  *out = L[id].info;
+  return LIFT_OK;
+}
+
+lift_status lift_variant_grid(int op, int id, int64_t n, int64_t* grid) {
+  if (op < 0 || op >= LIFT_NUM_OPS || !grid) return LIFT_ERR_INVALID_ARG;
+  if (!current_state()) return LIFT_ERR_NOT_INITIALIZED;
+  auto& L = registry(op);
+  if (id < 0 || id >= (int)L.size()) return LIFT_ERR_INVALID_ARG;
+  Args a;
+  a.n = n;
+  a.M = n;
+  a.N = 1;
+  *grid = L[id].grid(L[id], a);
+  return LIFT_OK;
+}
+
+lift_status lift_set_variant(int op, int variant) {
+  if (op < 0 || op >= LIFT_NUM_OPS) return LIFT_ERR_INVALID_ARG;
+  if (variant < -1 || variant >= (int)registry(op).size()) return LIFT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_policy_mu);
+  g_override[op] = variant;
+  return LIFT_OK;
+}
+
+// Table file: one line per entry "op log2(n+1) log2(M+1) log2(N+1) variant"
+// (gemv: n = M*N); '#' starts a comment.
+// MLP file: "lift-mlp 1 d_in h1 h2 V", then "offsets" and LIFT_NUM_OPS
+// integers, then W1 b1 W2 b2 W3 b3 as whitespace-separated floats
+// (W_k row-major [d_(k-1)][d_k]).
+lift_status lift_set_policy(int policy, const char* path) {
+  if (policy == LIFT_POLICY_FIXED) {
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    g_policy = policy;
+    return LIFT_OK;
+  }
+  if (!path) return set_error(LIFT_ERR_INVALID_ARG, "policy file path is NULL");
+  std::ifstream f(path);
+  if (!f) return set_error(LIFT_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  if (policy == LIFT_POLICY_TABLE) {
+    std::vector<TableEntry> T[LIFT_NUM_OPS];
+    std::string line;
+    while (std::getline(f, line)) {
+      if (line.empty() || line[0] == '#') continue;
+      std::istringstream is(line);
+      int op, v;
+      TableEntry e;
+      if (!(is >> op >> e.ln >> e.lm >> e.lN >> v)) continue;
+      if (op < 0 || op >= LIFT_NUM_OPS || v < 0 || v >= (int)registry(op).size())
+        return set_error(LIFT_ERR_INVALID_ARG, "table entry out of range");
+      e.variant = v;
+      T[op].push_back(e);
+    }
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    for (int i = 0; i < LIFT_NUM_OPS; ++i) g_table[i] = T[i];
+    g_policy = policy;
+    return LIFT_OK;
+  }
+  if (policy == LIFT_POLICY_MLP) {
+    Mlp m;
+    std::string tag, off;
+    int ver;
+    if (!(f >> tag >> ver >> m.d_in >> m.h1 >> m.h2 >> m.V) || tag != "lift-mlp" || m.d_in != 10)
+      return set_error(LIFT_ERR_INVALID_ARG, "bad MLP header");
+    if (!(f >> off) || off != "offsets") return set_error(LIFT_ERR_INVALID_ARG, "bad MLP offsets");
+    for (int i = 0; i < LIFT_NUM_OPS; ++i) f >> m.offsets[i];
+    auto rd = [&](std::vector<float>& w, size_t cnt) {
+      w.resize(cnt);
+      for (size_t i = 0; i < cnt; ++i)
+        if (!(f >> w[i])) return false;
+      return true;
+    };
+    if (!rd(m.W1, (size_t)m.d_in * m.h1) || !rd(m.b1, m.h1) || !rd(m.W2, (size_t)m.h1 * m.h2) ||
+        !rd(m.b2, m.h2) || !rd(m.W3, (size_t)m.h2 * m.V) || !rd(m.b3, m.V))
+      return set_error(LIFT_ERR_INVALID_ARG, "truncated MLP weights");
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    g_mlp = m;
+    g_policy = policy;
+    return LIFT_OK;
+  }
+  return set_error(LIFT_ERR_INVALID_ARG, "unknown policy");
+}
+
+lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant) {
+  if (op < 0 || op >= LIFT_NUM_OPS || !variant) return LIFT_ERR_INVALID_ARG;
+  if (registry(op).empty()) return LIFT_ERR_UNSUPPORTED;
+  *variant = pick_variant(op, n, M, N);
+  return LIFT_OK;
+}
+
+}  // extern "C"

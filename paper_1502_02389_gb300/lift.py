@@ -1,0 +1,239 @@
+"""Python binding of the liftblas C-ABI (``include/lift.h``).
+
+Argument marshalling only: every function has the name of its C entry
+point, takes the same arguments in the same order, and passes device
+pointers, sizes and a CUDA stream straight through.  Array arguments may be
+torch tensors (their ``data_ptr()`` is passed) or integer addresses; the
+stream defaults to torch's current stream.  A non-OK status raises
+``LiftError``.  There is no fallback: if the shared library is missing, the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liftblas.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NO_MEMORY, ERR_TIMEOUT, ERR_NOT_INITIALIZED = range(7)
+F32, BF16, FP8_E4M3 = 0, 1, 2
+OP_ASUM, OP_DOT, OP_SCAL, OP_GEMV, OP_ASUM_BF16, OP_DOT_BF16, OP_ASUM_FP8, OP_DOT_FP8 = range(8)
+NUM_OPS = 8
+OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8"]
+POLICY_FIXED, POLICY_TABLE, POLICY_MLP = 0, 1, 2
+
+
+class LiftError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({status_string(status)}) {detail}".strip())
+
+
+class VariantInfo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("op", "id", "tile", "vw", "threads", "stride", "tree",
+                                           "cluster", "passes", "stages", "rows", "lanes",
+                                           "final_threads")] + [("name", ctypes.c_char * 64)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "lift_init": ([ctypes.c_int], ctypes.c_int),
+    "lift_finalize": ([], ctypes.c_int),
+    "lift_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "lift_last_error": ([], ctypes.c_char_p),
+    "lift_sm_count": ([], ctypes.c_int),
+    "lift_read_status": ([ctypes.c_int], ctypes.c_int),
+    "lift_asum": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_dot": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "lift_scal": ([_I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
+    "lift_gemv": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
+    "lift_asum_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_dot_v": ([ctypes.c_int, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_scal_v": ([ctypes.c_int, _I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
+    "lift_gemv_v": ([ctypes.c_int, _I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P],
+                    ctypes.c_int),
+    "lift_variant_count": ([ctypes.c_int], ctypes.c_int),
+    "lift_variant_describe": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(VariantInfo)], ctypes.c_int),
+    "lift_variant_grid": ([ctypes.c_int, ctypes.c_int, _I64, ctypes.POINTER(_I64)], ctypes.c_int),
+    "lift_asum_ex": ([ctypes.c_int, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_dot_ex": ([ctypes.c_int, _P, _P, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_asum_ex_v": ([ctypes.c_int, ctypes.c_int, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_dot_ex_v": ([ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_set_policy": ([ctypes.c_int, ctypes.c_char_p], ctypes.c_int),
+    "lift_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lift_pick": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "lift_features": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load liftblas.so (built in-tree by ``paper_1502_02389_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1502_02389_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    return list(_SIGS)
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().lift_status_string(s).decode()
+    except Exception:  # the library itself may be what is missing
+        return "unknown"
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != OK:
+        raise LiftError(rc, where, lib().lift_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names and argument order as include/lift.h)
+# ---------------------------------------------------------------------------
+def lift_init(device: Optional[int] = None) -> None:
+    if device is None:
+        import torch
+        device = torch.cuda.current_device()
+    _check(lib().lift_init(device), "lift_init")
+
+
+def lift_finalize() -> None:
+    _check(lib().lift_finalize(), "lift_finalize")
+
+
+def lift_sm_count() -> int:
+    return lib().lift_sm_count()
+
+
+def lift_read_status(clear: bool = True) -> int:
+    return lib().lift_read_status(1 if clear else 0)
+
+
+def lift_asum(x, n, result, stream=None):
+    _check(lib().lift_asum(_ptr(x), n, _ptr(result), _stream(stream)), "lift_asum")
+
+
+def lift_dot(x, y, n, result, stream=None):
+    _check(lib().lift_dot(_ptr(x), _ptr(y), n, _ptr(result), _stream(stream)), "lift_dot")
+
+
+def lift_scal(n, alpha, x, y, stream=None):
+    _check(lib().lift_scal(n, alpha, _ptr(x), _ptr(y), _stream(stream)), "lift_scal")
+
+
+def lift_gemv(M, N, alpha, A, lda, x, beta, y, stream=None):
+    _check(lib().lift_gemv(M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y), _stream(stream)),
+           "lift_gemv")
+
+
+def lift_asum_v(variant, x, n, result, result_f64=None, stream=None):
+    _check(lib().lift_asum_v(variant, _ptr(x), n, _ptr(result), _ptr(result_f64), _stream(stream)),
+           "lift_asum_v")
+
+
+def lift_dot_v(variant, x, y, n, result, result_f64=None, stream=None):
+    _check(lib().lift_dot_v(variant, _ptr(x), _ptr(y), n, _ptr(result), _ptr(result_f64),
+                            _stream(stream)), "lift_dot_v")
+
+
+def lift_scal_v(variant, n, alpha, x, y, stream=None):
+    _check(lib().lift_scal_v(variant, n, alpha, _ptr(x), _ptr(y), _stream(stream)), "lift_scal_v")
+
+
+def lift_gemv_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
+    _check(lib().lift_gemv_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
+                             _stream(stream)), "lift_gemv_v")
+
+
+def lift_asum_ex(dtype, x, xscale, n, result, result_f64=None, stream=None):
+    _check(lib().lift_asum_ex(dtype, _ptr(x), _ptr(xscale), n, _ptr(result), _ptr(result_f64),
+                              _stream(stream)), "lift_asum_ex")
+
+
+def lift_dot_ex(dtype, x, xscale, y, yscale, n, result, result_f64=None, stream=None):
+    _check(lib().lift_dot_ex(dtype, _ptr(x), _ptr(xscale), _ptr(y), _ptr(yscale), n, _ptr(result),
+                             _ptr(result_f64), _stream(stream)), "lift_dot_ex")
+
+
+def lift_asum_ex_v(variant, dtype, x, xscale, n, result, result_f64=None, stream=None):
+    _check(lib().lift_asum_ex_v(variant, dtype, _ptr(x), _ptr(xscale), n, _ptr(result),
+                                _ptr(result_f64), _stream(stream)), "lift_asum_ex_v")
+
+
+def lift_dot_ex_v(variant, dtype, x, xscale, y, yscale, n, result, result_f64=None, stream=None):
+    _check(lib().lift_dot_ex_v(variant, dtype, _ptr(x), _ptr(xscale), _ptr(y), _ptr(yscale), n,
+                               _ptr(result), _ptr(result_f64), _stream(stream)), "lift_dot_ex_v")
+
+
+def lift_variant_count(op: int) -> int:
+    return lib().lift_variant_count(op)
+
+
+def lift_variant_describe(op: int, vid: int) -> Dict:
+    info = VariantInfo()
+    _check(lib().lift_variant_describe(op, vid, ctypes.byref(info)), "lift_variant_describe")
+    d = {k: getattr(info, k) for k, _ in VariantInfo._fields_ if k != "name"}
+    d["name"] = info.name.decode()
+    return d
+
+
+def lift_variant_grid(op: int, vid: int, n: int) -> int:
+    g = _I64()
+    _check(lib().lift_variant_grid(op, vid, n, ctypes.byref(g)), "lift_variant_grid")
+    return g.value
+
+
+def lift_set_policy(policy: int, path: Optional[str] = None) -> None:
+    _check(lib().lift_set_policy(policy, path.encode() if path else None), "lift_set_policy")
+
+
+def lift_set_variant(op: int, variant: int) -> None:
+    _check(lib().lift_set_variant(op, variant), "lift_set_variant")
+
+
+def lift_pick(op: int, n: int, M: int = 0, N: int = 0) -> int:
+    v = ctypes.c_int()
+    _check(lib().lift_pick(op, n, M, N, ctypes.byref(v)), "lift_pick")
+    return v.value
+
+
+def lift_features(op: int, n: int, M: int = 0, N: int = 0) -> List[float]:
+    out = (ctypes.c_float * 10)()
+    _check(lib().lift_features(op, n, M, N, out), "lift_features")
+    return list(out)
+
+
+def variants(op: int) -> List[Dict]:
+    return [lift_variant_describe(op, i) for i in range(lift_variant_count(op))]
