@@ -209,6 +209,35 @@ lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
  * size feature uses n = M*N.  Host-only; needs no device. */
 lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out);
 
+/* ------------------------------------------------------------------------
+ * Cost-model training kernels (FP32).  A multilayer perceptron
+ * d_in -> h1 -> h2 -> V (ReLU hidden layers) predicts one log-time per
+ * kernel variant from the features of a call (lift_features); it replaces
+ * the paper's empirical choice of split sizes and vector widths (Sec. 6.2,
+ * and the model-guided search Sec. 6.3 names as future work).
+ * All pointers are device pointers owned by the caller; fp32, row-major.
+ *   params: W1[d_in][h1] b1[h1] W2[h1][h2] b2[h2] W3[h2][V] b3[V]
+ *           (lift_mlp_param_count floats; grads, Adam m and v: same layout)
+ *   X: B x d_in features; P: B x V predictions; T, mask: B x V targets and
+ *   0/1 weights; work: lift_mlp_work_count(B, h1, h2) floats that hold the
+ *   forward activations for the backward pass (Z1 H1 Z2 H2, then two
+ *   B x max(h1,h2) gradient buffers).
+ * loss = sum(mask * (P - T)^2) * inv_measured (inv_measured = 1 / sum(mask));
+ * dP = 2 * mask * (P - T) * inv_measured; Adam as in Kingma and Ba (2015)
+ * with bias correction at step t >= 1.
+ * ------------------------------------------------------------------------ */
+int64_t lift_mlp_param_count(int d_in, int h1, int h2, int V);
+int64_t lift_mlp_work_count(int64_t B, int h1, int h2);
+lift_status lift_mlp_forward(int d_in, int h1, int h2, int V, const float* params, const float* X,
+                             int64_t B, float* work, float* P, void* stream);
+lift_status lift_mlp_loss(const float* P, const float* T, const float* mask, int64_t count,
+                          float inv_measured, float* dP, float* loss, void* stream);
+lift_status lift_mlp_backward(int d_in, int h1, int h2, int V, const float* params,
+                              const float* X, int64_t B, float* work, const float* dP,
+                              float* grads, void* stream);
+lift_status lift_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t count,
+                          int t, float lr, float beta1, float beta2, float eps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,185 @@
+"""Variant cost model: an MLP that proposes the kernel variant for a call.
+
+The paper fixes the integer parameters of each device's expression by
+exploring values empirically (Sec. 6.2) and names a model-guided search as
+future work (Sec. 6.3).  Here the autotuner's measurements (``tune.py``)
+train a small network that maps the features of a call (``lift_features``:
+op family, log2 sizes, element type) to one predicted value per kernel
+variant: the log of the variant's time relative to the fastest variant of
+that shape.  The library's MLP policy picks the argmin over the op's
+variants; exhaustive autotuning stays the fallback and the judge of the
+pick's regret t(pick) / t(best).
+
+Training runs on the GPU through the library's own kernels
+(``lift_mlp_forward`` / ``_loss`` / ``_backward`` / ``_adam``); this module
+only arranges the data and calls them.
+"""
+from __future__ import annotations
+
+import math
+from collections import defaultdict
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import lift
+
+D_IN, H1, H2 = 10, 64, 64
+
+
+def offsets() -> Tuple[List[int], int]:
+    """Output index of each op's variant 0, and the total output width V."""
+    off, v = [], 0
+    for op in range(lift.NUM_OPS):
+        off.append(v)
+        v += lift.lift_variant_count(op)
+    return off, v
+
+
+def group(records: List[Dict]) -> Dict[Tuple[int, int, int, int], Dict[int, float]]:
+    """(op, n, M, N) -> {variant: ms}"""
+    g: Dict = defaultdict(dict)
+    for r in records:
+        g[(r["op"], r["n"], r["M"], r["N"])][r["variant"]] = r["ms"]
+    return g
+
+
+def dataset(records: List[Dict]):
+    """Features X [B, 10], targets T [B, V] = log(t_v / t_best), mask M."""
+    off, V = offsets()
+    g = group(records)
+    keys = sorted(g)
+    X = np.zeros((len(keys), D_IN), np.float32)
+    T = np.zeros((len(keys), V), np.float32)
+    M = np.zeros((len(keys), V), np.float32)
+    for i, k in enumerate(keys):
+        op, n, Mm, N = k
+        X[i] = lift.lift_features(op, n, Mm, N)
+        times = g[k]
+        best = min(times.values())
+        for v, ms in times.items():
+            T[i, off[op] + v] = math.log(ms / best)
+            M[i, off[op] + v] = 1.0
+    return keys, X, T, M
+
+
+def init_params(V: int, seed: int = 0) -> np.ndarray:
+    """He-initialised weights, zero biases, in the library's flat layout."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.standard_normal((D_IN, H1)) * math.sqrt(2.0 / D_IN), np.zeros(H1),
+             rng.standard_normal((H1, H2)) * math.sqrt(2.0 / H1), np.zeros(H2),
+             rng.standard_normal((H2, V)) * math.sqrt(1.0 / H2), np.zeros(V)]
+    flat = np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+    assert flat.size == lift.lift_mlp_param_count(D_IN, H1, H2, V)
+    return flat
+
+
+def unflatten(flat: np.ndarray, V: int) -> Dict[str, np.ndarray]:
+    shapes = [("W1", (D_IN, H1)), ("b1", (H1,)), ("W2", (H1, H2)), ("b2", (H2,)),
+              ("W3", (H2, V)), ("b3", (V,))]
+    out, o = {}, 0
+    for name, shp in shapes:
+        c = int(np.prod(shp))
+        out[name] = np.asarray(flat[o:o + c], np.float64).reshape(shp)
+        o += c
+    return out
+
+
+class Trainer:
+    """Full-batch Adam on the GPU with the library's MLP kernels."""
+
+    def __init__(self, X: np.ndarray, T: np.ndarray, M: np.ndarray, seed: int = 0,
+                 params: Optional[np.ndarray] = None):
+        import torch
+        self.torch = torch
+        self.B, self.V = T.shape
+        dev = "cuda"
+        self.X = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+        self.T = torch.from_numpy(np.ascontiguousarray(T)).to(dev)
+        self.M = torch.from_numpy(np.ascontiguousarray(M)).to(dev)
+        self.inv = float(1.0 / max(1.0, M.sum()))
+        p = init_params(self.V, seed) if params is None else params
+        self.p = torch.from_numpy(p.copy()).to(dev)
+        self.count = self.p.numel()
+        self.g = torch.zeros_like(self.p)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.work = torch.zeros(lift.lift_mlp_work_count(self.B, H1, H2), device=dev)
+        self.P = torch.zeros((self.B, self.V), device=dev)
+        self.dP = torch.zeros_like(self.P)
+        self.loss = torch.zeros(1, device=dev)
+        self.t = 0
+
+    def forward(self):
+        lift.lift_mlp_forward(D_IN, H1, H2, self.V, self.p, self.X, self.B, self.work, self.P)
+        return self.P
+
+    def grads(self):
+        """Loss and parameter gradients at the current parameters."""
+        self.forward()
+        lift.lift_mlp_loss(self.P, self.T, self.M, self.B * self.V, self.inv, self.dP, self.loss)
+        lift.lift_mlp_backward(D_IN, H1, H2, self.V, self.p, self.X, self.B, self.work, self.dP,
+                               self.g)
+        return self.loss, self.g
+
+    def step(self, lr: float):
+        self.grads()
+        self.t += 1
+        lift.lift_mlp_adam(self.p, self.g, self.m, self.v, self.count, self.t, lr, 0.9, 0.999, 1e-8)
+
+    def train(self, steps: int = 4000, lr: float = 3e-3, log_every: int = 0) -> List[float]:
+        hist = []
+        for i in range(steps):
+            frac = i / max(1, steps - 1)
+            self.step(lr * (0.1 + 0.9 * 0.5 * (1 + math.cos(math.pi * frac))))
+            if log_every and (i % log_every == 0 or i == steps - 1):
+                hist.append(float(self.loss.item()))
+        self.torch.cuda.synchronize()
+        return hist
+
+    def params(self) -> np.ndarray:
+        return self.p.cpu().numpy()
+
+
+def save(path: str, params: np.ndarray, V: int) -> None:
+    """Weights file read by lift_set_policy(LIFT_POLICY_MLP, path)."""
+    off, _ = offsets()
+    with open(path, "w") as f:
+        f.write(f"lift-mlp 1 {D_IN} {H1} {H2} {V}\n")
+        f.write("offsets " + " ".join(str(o) for o in off) + "\n")
+        f.write(" ".join(f"{x:.9g}" for x in params.tolist()) + "\n")
+
+
+# ---------------------------------------------------------------------------
+# regret
+# ---------------------------------------------------------------------------
+def regrets(records: List[Dict], pick) -> np.ndarray:
+    """t(pick(shape)) / t(best) over the shapes of an exhaustive sweep."""
+    out = []
+    for (op, n, M, N), times in sorted(group(records).items()):
+        v = pick(op, n, M, N)
+        out.append(times[v] / min(times.values()))
+    return np.asarray(out)
+
+
+def summary(r: np.ndarray) -> Dict[str, float]:
+    return {"geomean": float(np.exp(np.mean(np.log(r)))), "p90": float(np.percentile(r, 90)),
+            "max": float(r.max()), "shapes": int(r.size)}
+
+
+def best_fixed(records: List[Dict]) -> Dict[int, int]:
+    """Per op, the single variant with the smallest geomean time ratio over
+    the given shapes (the paper's one fixed derivation per device)."""
+    g = group(records)
+    best = {}
+    for op in range(lift.NUM_OPS):
+        rows = [t for (o, *_), t in g.items() if o == op]
+        if not rows:
+            continue
+        cnt = lift.lift_variant_count(op)
+        score = []
+        for v in range(cnt):
+            if all(v in t for t in rows):
+                score.append((np.mean([math.log(t[v] / min(t.values())) for t in rows]), v))
+        best[op] = min(score)[1]
+    return best

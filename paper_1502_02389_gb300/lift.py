@@ -66,6 +66,12 @@ _SIGS = {
     "lift_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "lift_pick": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lift_features": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "lift_mlp_param_count": ([ctypes.c_int] * 4, _I64),
+    "lift_mlp_work_count": ([_I64, ctypes.c_int, ctypes.c_int], _I64),
+    "lift_mlp_forward": ([ctypes.c_int] * 4 + [_P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_mlp_loss": ([_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
+    "lift_mlp_backward": ([ctypes.c_int] * 4 + [_P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "lift_mlp_adam": ([_P, _P, _P, _P, _I64, ctypes.c_int] + [ctypes.c_float] * 4 + [_P], ctypes.c_int),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -233,6 +239,34 @@ def lift_features(op: int, n: int, M: int = 0, N: int = 0) -> List[float]:
     out = (ctypes.c_float * 10)()
     _check(lib().lift_features(op, n, M, N, out), "lift_features")
     return list(out)
+
+
+def lift_mlp_param_count(d_in, h1, h2, V) -> int:
+    return lib().lift_mlp_param_count(d_in, h1, h2, V)
+
+
+def lift_mlp_work_count(B, h1, h2) -> int:
+    return lib().lift_mlp_work_count(B, h1, h2)
+
+
+def lift_mlp_forward(d_in, h1, h2, V, params, X, B, work, P, stream=None):
+    _check(lib().lift_mlp_forward(d_in, h1, h2, V, _ptr(params), _ptr(X), B, _ptr(work), _ptr(P),
+                                  _stream(stream)), "lift_mlp_forward")
+
+
+def lift_mlp_loss(P, T, mask, count, inv_measured, dP, loss, stream=None):
+    _check(lib().lift_mlp_loss(_ptr(P), _ptr(T), _ptr(mask), count, inv_measured, _ptr(dP),
+                               _ptr(loss), _stream(stream)), "lift_mlp_loss")
+
+
+def lift_mlp_backward(d_in, h1, h2, V, params, X, B, work, dP, grads, stream=None):
+    _check(lib().lift_mlp_backward(d_in, h1, h2, V, _ptr(params), _ptr(X), B, _ptr(work), _ptr(dP),
+                                   _ptr(grads), _stream(stream)), "lift_mlp_backward")
+
+
+def lift_mlp_adam(params, grads, m, v, count, t, lr, beta1, beta2, eps, stream=None):
+    _check(lib().lift_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), count, t, lr, beta1,
+                               beta2, eps, _stream(stream)), "lift_mlp_adam")
 
 
 def variants(op: int) -> List[Dict]:

@@ -2,11 +2,13 @@
 
 The paper chooses its split sizes and vector widths "by exploring different
 values empirically" (Sec. 6.2); this module does that exploration on the
-device.  For each (op, shape) it launches every variant through the C-ABI,
-times it with CUDA events on the launching stream (median of ``reps`` after
-``warmup`` calls; the L2 is flushed by reading a 512 MiB buffer before each
-timed call when the working set is below twice the L2 size), and appends one
-JSON record per (device, op, shape, variant) to a database file.  Records
+device.  For each (op, shape) it launches every variant through the C-ABI
+and times it with CUDA events on the launching stream: a CUDA graph of R
+back-to-back calls (R disjoint input slices when the working set is below
+twice the L2 size, so every call reads cold data from HBM; R = 1 otherwise)
+is replayed ``reps`` times and the median replay time divided by R is the
+per-call time.  One JSON record per (device, op, shape, variant) is appended
+to a database file.  Records
 already present are skipped, so an interrupted sweep resumes where it
 stopped.  ``write_table`` turns a database into the nearest-shape table the
 TABLE policy of the library reads.
@@ -50,80 +52,125 @@ def device_key() -> str:
     return f"{p.name}|sm{p.multi_processor_count}"
 
 
-class Buffers:
-    """Device inputs of one shape (random contents; timing does not depend
-    on the values)."""
+POOL_BYTES = 1 << 30   # rotation pool: every call of a small shape reads cold data
+MAX_ROT = 64
 
-    def __init__(self, op: int, n: int, M: int, N: int, seed: int = 0):
+
+def rotation(nbytes: int) -> int:
+    """Calls in one timed graph: 1 for working sets of at least twice the
+    L2 (they are cold anyway), else enough distinct slices of a 1 GiB pool
+    that a slice is evicted before it is read again."""
+    if nbytes >= 2 * L2_BYTES:
+        return 1
+    return int(max(2, min(MAX_ROT, POOL_BYTES // max(nbytes, 1))))
+
+
+class Pools:
+    """1 GiB device arrays (random contents) that every shape slices; the
+    R slices of a call rotation sit POOL_BYTES / R apart, so the R calls of
+    a small shape together touch more than the L2 holds."""
+
+    def __init__(self, seed: int = 0):
         import torch
-        g = torch.Generator(device="cuda")
-        g.manual_seed(seed)
-        self.op, self.n, self.M, self.N = op, n, M, N
-        dev = "cuda"
-        self.r = torch.zeros(1, device=dev)
-        if op in (lift.OP_ASUM, lift.OP_DOT, lift.OP_SCAL):
-            self.x = torch.randn(max(n, 1), device=dev, generator=g)
-            self.y = torch.randn(max(n, 1), device=dev, generator=g) if op != lift.OP_ASUM else None
-        elif op == lift.OP_GEMV:
-            self.A = torch.randn(max(M * N, 1), device=dev, generator=g)
-            self.x = torch.randn(max(N, 1), device=dev, generator=g)
-            self.y = torch.randn(max(M, 1), device=dev, generator=g)
-        else:
-            nbytes = n * (2 if op in (lift.OP_ASUM_BF16, lift.OP_DOT_BF16) else 1)
-            # bf16: draw N(0,1) values and keep their bf16 bits; fp8: bytes
-            # below 0x7F / 0xFF avoid the NaN codes
-            if op in (lift.OP_ASUM_BF16, lift.OP_DOT_BF16):
-                self.x = torch.randn(max(n, 1), device=dev, generator=g).to(torch.bfloat16)
-                self.y = torch.randn(max(n, 1), device=dev, generator=g).to(torch.bfloat16)
-            else:
-                self.x = torch.randint(0, 0x7E, (max(nbytes, 1),), device=dev, generator=g,
-                                       dtype=torch.uint8)
-                self.y = torch.randint(0, 0x7E, (max(nbytes, 1),), device=dev, generator=g,
-                                       dtype=torch.uint8)
-            nb = max(1, math.ceil(n / 4096))
-            self.xs = torch.rand(nb, device=dev, generator=g) + 0.5
-            self.ys = torch.rand(nb, device=dev, generator=g) + 0.5
+        self.torch = torch
+        self.g = torch.Generator(device="cuda")
+        self.g.manual_seed(seed)
+        self.cache = {}
 
-    def call(self, vid: int):
-        op, n = self.op, self.n
+    def get(self, name: str, kind: str):
+        if name not in self.cache:
+            t, g = self.torch, self.g
+            if kind == "f32":
+                a = t.randn(POOL_BYTES // 4, device="cuda", generator=g)
+            elif kind == "bf16":
+                a = t.randn(POOL_BYTES // 2, device="cuda", generator=g).to(t.bfloat16)
+            elif kind == "u8":   # E4M3 codes below 0x7E: finite values, no NaN
+                a = t.randint(0, 0x7E, (POOL_BYTES,), device="cuda", generator=g, dtype=t.uint8)
+            else:                # block scales
+                a = t.rand(1 << 20, device="cuda", generator=g) + 0.5
+            self.cache[name] = a
+        return self.cache[name]
+
+
+class Buffers:
+    """Slices of the pools for one shape: R disjoint, evenly spread slices
+    of each array (timing does not depend on the values)."""
+
+    def __init__(self, pools: Pools, op: int, n: int, M: int, N: int):
+        self.op, self.n, self.M, self.N = op, n, M, N
+        self.R = rotation(op_bytes(op, n, M, N))
+        self.pools = pools
+        self.res = pools.torch.zeros(self.R * 64, device="cuda")
+
+    def _slice(self, name, kind, r, count):
+        a = self.pools.get(name, kind)
+        stride = (a.numel() // self.R) // 256 * 256
+        assert count <= stride or self.R == 1, "slice larger than its share of the pool"
+        assert count <= a.numel()
+        return a[r * stride: r * stride + count]
+
+    def call(self, vid: int, r: int):
+        """The r-th call of the rotation for variant vid."""
+        op, n, M, N = self.op, self.n, self.M, self.N
+        res = self.res[64 * r:64 * r + 1]
         if op == lift.OP_ASUM:
-            return lambda: lift.lift_asum_v(vid, self.x, n, self.r)
+            x = self._slice("x", "f32", r, n)
+            return lambda: lift.lift_asum_v(vid, x, n, res)
         if op == lift.OP_DOT:
-            return lambda: lift.lift_dot_v(vid, self.x, self.y, n, self.r)
+            x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
+            return lambda: lift.lift_dot_v(vid, x, y, n, res)
         if op == lift.OP_SCAL:
-            return lambda: lift.lift_scal_v(vid, n, 1.5, self.x, self.y)
+            x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
+            return lambda: lift.lift_scal_v(vid, n, 1.5, x, y)
         if op == lift.OP_GEMV:
-            return lambda: lift.lift_gemv_v(vid, self.M, self.N, 1.0, self.A, self.N, self.x, 0.5,
-                                            self.y)
-        dt = lift.BF16 if op in (lift.OP_ASUM_BF16, lift.OP_DOT_BF16) else lift.FP8_E4M3
-        xs = self.xs if dt == lift.FP8_E4M3 else None
-        ys = self.ys if dt == lift.FP8_E4M3 else None
+            A = self._slice("x", "f32", r, M * N)
+            y = self._slice("y", "f32", r, M)
+            xv = self._slice("gx", "f32", 0, N)
+            return lambda: lift.lift_gemv_v(vid, M, N, 1.0, A, N, xv, 0.5, y)
+        bf = op in (lift.OP_ASUM_BF16, lift.OP_DOT_BF16)
+        dt = lift.BF16 if bf else lift.FP8_E4M3
+        kind = "bf16" if bf else "u8"
+        x, y = self._slice("x" + kind, kind, r, n), self._slice("y" + kind, kind, r, n)
+        nb = max(1, math.ceil(n / 4096))
+        xs = None if bf else self.pools.get("xs", "scale")[:nb]
+        ys = None if bf else self.pools.get("ys", "scale")[:nb]
         if op in (lift.OP_ASUM_BF16, lift.OP_ASUM_FP8):
-            return lambda: lift.lift_asum_ex_v(vid, dt, self.x, xs, n, self.r)
-        return lambda: lift.lift_dot_ex_v(vid, dt, self.x, xs, self.y, ys, n, self.r)
+            return lambda: lift.lift_asum_ex_v(vid, dt, x, xs, n, res)
+        return lambda: lift.lift_dot_ex_v(vid, dt, x, xs, y, ys, n, res)
 
 
 class Timer:
+    """Time R calls captured in one CUDA graph; a replay runs the calls back
+    to back on one stream, so the host's launch overhead and the event
+    resolution do not enter the per-call time."""
+
     def __init__(self):
         import torch
         self.torch = torch
-        self.flush_buf = torch.ones(128 << 20, device="cuda")   # 512 MiB
 
-    def median_ms(self, fn, reps: int, warmup: int, flush: bool) -> float:
+    def per_call_ms(self, calls, reps: int, warmup: int) -> float:
         torch = self.torch
         for _ in range(warmup):
-            fn()
+            for c in calls:
+                c()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for c in calls:
+                c()
+        g.replay()
+        torch.cuda.synchronize()
         s = torch.cuda.current_stream()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(reps)]
         for a, b in ev:
-            if flush:
-                self.flush_buf.sum()
             a.record(s)
-            fn()
+            g.replay()
             b.record(s)
         torch.cuda.synchronize()
-        return statistics.median(a.elapsed_time(b) for a, b in ev)
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev) / len(calls)
+        del g
+        return ms
 
 
 def _key(rec) -> Tuple:
@@ -151,6 +198,7 @@ def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], r
     dkey = device_key()
     done = {_key(r) for r in load_db(db_path)} if db_path else set()
     timer = Timer()
+    pools = Pools()
     out = []
     f = open(db_path, "a") if db_path else None
     try:
@@ -160,15 +208,14 @@ def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], r
             todo = [v for v in vids if (dkey, op, n, M, N, v) not in done]
             if not todo:
                 continue
-            buf = Buffers(op, n, M, N)
+            buf = Buffers(pools, op, n, M, N)
             nbytes = op_bytes(op, n, M, N)
-            flush = nbytes < 2 * L2_BYTES
             for v in todo:
-                ms = timer.median_ms(buf.call(v), reps, warmup, flush)
+                ms = timer.per_call_ms([buf.call(v, r) for r in range(buf.R)], reps, warmup)
                 rec = {"device": dkey, "op": op, "opname": lift.OP_NAMES[op], "n": n, "M": M,
                        "N": N, "variant": v, "name": lift.lift_variant_describe(op, v)["name"],
                        "ms": ms, "bytes": nbytes, "gbs": nbytes / (ms * 1e-3) / 1e9,
-                       "reps": reps, "flushed": flush}
+                       "reps": reps, "rotation": buf.R}
                 out.append(rec)
                 if f:
                     f.write(json.dumps(rec) + "\n")
@@ -180,7 +227,6 @@ def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], r
                 print(f"{lift.OP_NAMES[op]:10s} n={n} M={M} N={N}: best {best['name']} "
                       f"{best['ms'] * 1e3:.1f} us {best['gbs']:.0f} GB/s", flush=True)
             del buf
-            torch.cuda.empty_cache()
     finally:
         if f:
             f.close()
