@@ -238,6 +238,27 @@ lift_status lift_mlp_backward(int d_in, int h1, int h2, int V, const float* para
 lift_status lift_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t count,
                           int t, float lr, float beta1, float beta2, float eps, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free asum.  The paper has no counterpart: this entry point
+ * exists for callers that must not have the library allocate device memory
+ * -- a process whose device memory belongs to its own pool allocator under
+ * a fixed budget, or a latency-critical loop that cannot pay for cudaFree's
+ * device-wide synchronisation.  It computes what lift_asum computes (x: n
+ * floats, result: one float, both device pointers owned by the caller) and
+ * needs no lift_init: its scratch (4096 fp32 partial slots and one ticket
+ * word, about 16 KiB) is a fixed array inside the library's device image,
+ * held on every GPU that loads the library until the process exits.
+ *  - The first call on a device looks up that array's address (with the
+ *    device current) and caches it: make the first call before any stream
+ *    capture.
+ *  - Every call shares the array.  Each call clears the ticket on `stream`
+ *    before its kernel; calls whose kernels overlap on the GPU race and
+ *    give wrong results, so order them.
+ *  - A launch that would need more than 4096 partial slots returns
+ *    LIFT_ERR_UNSUPPORTED; invalid arguments return LIFT_ERR_INVALID_ARG.
+ * ------------------------------------------------------------------------ */
+lift_status lift_asum_noalloc(const float* x, int64_t n, float* result, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

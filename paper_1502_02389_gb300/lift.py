@@ -66,6 +66,7 @@ _SIGS = {
     "lift_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "lift_pick": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lift_features": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "lift_asum_noalloc": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_mlp_param_count": ([ctypes.c_int] * 4, _I64),
     "lift_mlp_work_count": ([_I64, ctypes.c_int, ctypes.c_int], _I64),
     "lift_mlp_forward": ([ctypes.c_int] * 4 + [_P, _P, _I64, _P, _P, _P], ctypes.c_int),
@@ -239,6 +240,10 @@ def lift_features(op: int, n: int, M: int = 0, N: int = 0) -> List[float]:
     out = (ctypes.c_float * 10)()
     _check(lib().lift_features(op, n, M, N, out), "lift_features")
     return list(out)
+
+
+def lift_asum_noalloc(x, n, result, stream=None):
+    _check(lib().lift_asum_noalloc(_ptr(x), n, _ptr(result), _stream(stream)), "lift_asum_noalloc")
 
 
 def lift_mlp_param_count(d_in, h1, h2, V) -> int:
