@@ -48,21 +48,31 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def csrc_hash() -> str:
-    h = hashlib.sha256()
+KERNEL_SOURCE = {"asum": "reduce_f32.cu", "dot": "reduce_f32.cu", "scal": "scal_gemv.cu",
+                 "gemv": "scal_gemv.cu", "batch": "batch.cu"}
+
+
+def kernel_hash(tag: str) -> str:
+    """Hash of the source of the kernel a tag names (its .cu file and the
+    shared device header): ncu counters taken on other sources are stale."""
+    op = tag.split("_", 1)[0]
     d = os.path.join(ROOT, "paper_1502_02389_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    h = hashlib.sha256()
+    for f in (KERNEL_SOURCE.get(op, ""), "lift_internal.cuh"):
+        p = os.path.join(d, f)
+        if f and os.path.exists(p):
+            h.update(open(p, "rb").read())
     return h.hexdigest()[:12]
 
 
 def traffic_for(kernel_tag: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources ('tag hash bytes' lines)."""
+    """DRAM bytes per launch (read + write) from the committed ncu summary,
+    when it was taken on the current source of that kernel
+    ('variant-name source-hash bytes' lines of profiles/traffic.txt)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    want = csrc_hash()
+    want = kernel_hash(kernel_tag)
     for line in open(p):
         f = line.split()
         if len(f) == 3 and f[0] == kernel_tag and f[1] == want:
