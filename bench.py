@@ -37,6 +37,9 @@ WORKLOADS = {
     "asum": dict(n=1 << 20, desc="asum(x) fp32, n=2^20, U(-1,1) seed 0, L2 flushed per step"),
     "gemv_square": dict(M=8192, N=8192, desc="gemv fp32 8192x8192, alpha=1, beta=0.5, seed 2"),
     "gemv_tall": dict(M=65536, N=1024, desc="gemv fp32 65536x1024, alpha=1, beta=0.5, seed 2"),
+    "batch": dict(desc="batched launch: 20,000 ops (asum/dot/gemv, lengths 2^U(8,22), "
+                       "gemv M,N 2^U(6,12)), about 60 GB, seed 3, one graph-launched "
+                       "persistent kernel"),
 }
 
 
@@ -224,6 +227,76 @@ def run_ours(args, rank, world, dist):
         h2d, d2h = 4 * n, 4
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
                   "l2": "flushed before every step (a 512 MiB read, outside the kernel events)"}
+    elif wl == "batch":
+        from paper_1502_02389_gb300 import costmodel
+        ops = synth.batch_ops()
+        lay, total = synth.batch_layout(ops)
+        g = torch.Generator(device=dev)
+        g.manual_seed(3)
+        pool = torch.randn(total, device=dev, generator=g)
+        base = pool.data_ptr()
+        descs = []
+        for d, e in zip(ops, lay):
+            q = {"op": d["op"], "variant": -1, "n": d["n"], "M": d["M"], "N": d["N"],
+                 "lda": d["N"], "alpha": 1.0, "beta": 0.5, "out": base + 4 * e["out"]}
+            for k in ("x", "y", "A"):
+                if k in e:
+                    q[k] = base + 4 * e[k]
+            descs.append(q)
+        policies = {"fixed": (lift.POLICY_FIXED, None)}
+        table = os.path.join(ROOT, "gpurun_out", "bench_table.txt")
+        try:
+            from paper_1502_02389_gb300 import tune
+            recs = tune.load_csv(os.path.join(costmodel.DATA, "timings_gb300_train.csv"))
+            os.makedirs(os.path.dirname(table), exist_ok=True)
+            tune.write_table(recs, table)
+            policies["table"] = (lift.POLICY_TABLE, table)
+        except (OSError, AssertionError):
+            pass
+        weights = args.mlp or costmodel.WEIGHTS
+        if os.path.exists(weights):
+            policies["mlp"] = (lift.POLICY_MLP, weights)
+        handles = {}
+        for name, (pol, path) in policies.items():
+            lift.lift_set_policy(pol, path)
+            handles[name] = lift.lift_batch_create(descs)
+        lift.lift_set_policy(lift.POLICY_FIXED)
+        main_policy = "mlp" if "mlp" in handles else "fixed"
+        hb = handles[main_policy]
+        info = lift.lift_batch_info(hb)
+        bytes_step = info["bytes"]
+        launches_per_step = 1
+        kb = ["batch:" + main_policy, bytes_step, [], []]
+        kernels = [kb]
+
+        def step(timed):
+            if timed:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(s)
+            lift.lift_batch_run(hb)
+            if timed:
+                ev[1].record(s)
+                kb[2].append(ev[0]); kb[3].append(ev[1])
+
+        # the other policies, timed the same way after the main measurement
+        def policy_rates():
+            out = {}
+            for name, h in handles.items():
+                for _ in range(2):
+                    lift.lift_batch_run(h)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                for _ in range(5):
+                    lift.lift_batch_run(h)
+                b.record(s)
+                torch.cuda.synchronize()
+                out[name] = round(bytes_step * 5 / (a.elapsed_time(b) / 1e3) / 1e9, 1)
+            return out
+
+        e2e_step, host, h2d, d2h = None, {}, 0, 0
+        config = {"workload": WORKLOADS[wl]["desc"], "ops": len(ops), "items": info["items"],
+                  "grid": info["grid"], "policy": main_policy,
+                  "l2": "no flush: every run reads about 60 GB, far beyond the 129 MB L2"}
     else:
         M, N = WORKLOADS[wl]["M"], WORKLOADS[wl]["N"]
         Ah, xh, yh, a, b = synth.gemv(M, N)
@@ -296,23 +369,29 @@ def run_ours(args, rank, world, dist):
             "algorithmic_bytes_per_launch": kernels[[k[0] for k in kernels].index(dom)][1]}
 
     # ---- end to end through the C-ABI with host buffers
-    for _ in range(2):
-        e2e_step(**host)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ek = max(3, min(args.steps, 10))
-    e0.record(s)
-    for _ in range(ek):
-        e2e_step(**host)
-    e1.record(s)
-    torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1) / ek
-    if dist:
-        t = torch.tensor([ems], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
-    e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
+    e2e = None
+    if e2e_step is not None:
+        for _ in range(2):
+            e2e_step(**host)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ek = max(3, min(args.steps, 10))
+        e0.record(s)
+        for _ in range(ek):
+            e2e_step(**host)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / ek
+        if dist:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
+    if wl == "batch":
+        config["policies_gbs"] = policy_rates()
+        for h in handles.values():
+            lift.lift_batch_destroy(h)
     assert lift.lift_read_status() == 0
     return dict(value=value, ms_step=ms_step, roofline=roof, per_kernel=per_kernel, clocks=clk,
                 e2e=e2e, config=config, launches=launches_per_step * args.steps, peak=peak)
@@ -340,6 +419,29 @@ def oracle_sample(workload: str, budget_s: float):
         x = synth.asum_small(n)
         work = lambda: blas.asum(x)  # noqa: E731
         bytes_one, what = 4 * n, "full step (asum, n=2^20)"
+    elif workload == "batch":
+        ops = synth.batch_ops()[:400]
+        rng = np.random.default_rng(3)
+        arrays = []
+        for d in ops:
+            if d["op"] == synth.GEMV:
+                arrays.append((d, rng.standard_normal((d["M"], d["N"])), rng.standard_normal(d["N"]),
+                               rng.standard_normal(d["M"])))
+            else:
+                arrays.append((d, rng.standard_normal(d["n"]),
+                               rng.standard_normal(d["n"]) if d["op"] == synth.DOT else None, None))
+
+        def work():
+            for d, a1, a2, a3 in arrays:
+                if d["op"] == synth.GEMV:
+                    blas.gemv(a1, a2, a3, 1.0, 0.5)
+                elif d["op"] == synth.DOT:
+                    blas.dot(a1, a2)
+                else:
+                    blas.asum(a1)
+        bytes_one = sum(4 * d["M"] * d["N"] + 4 * d["N"] + 8 * d["M"] if d["op"] == synth.GEMV
+                        else (8 if d["op"] == synth.DOT else 4) * d["n"] for d in ops)
+        what = "first 400 of the 20,000 batch ops (same op/size draws, host values)"
     else:
         M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
         A, xv, yv, a, b = synth.gemv(M, N)
@@ -382,6 +484,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dot_scal", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mlp", default=None, help="cost-model weights for the batch workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

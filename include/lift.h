@@ -210,6 +210,60 @@ lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
 lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out);
 
 /* ------------------------------------------------------------------------
+ * Batched persistent launch: many asum / dot / scal / gemv calls of uneven
+ * sizes in one graph-launched persistent kernel with a work queue (map over
+ * the batch lowered to map-workgroup over work items).
+ *
+ * lift_op_desc: one call, with the arguments of the matching single-op
+ * entry point (device pointers owned by the caller, valid while the batch
+ * runs).  asum / dot: x (and y) of n floats, out = one float.  scal:
+ * out[i] = alpha * x[i], n floats.  gemv: out <- alpha * A x + beta * out,
+ * A row-major M x N with lda >= N, x of N floats, out of M floats (read
+ * only when beta != 0).  variant: a variant id of that op whose tile and
+ * vector width the batch adopts, or -1 for the current policy's pick
+ * (FIXED, TABLE or MLP) at creation time.
+ *
+ * lift_batch_create validates every descriptor (op id, variant id, sizes,
+ * NULL or unaligned pointers) before touching the device and returns
+ * LIFT_ERR_INVALID_ARG naming the first bad op; it then splits each op into
+ * work items of about 256 KiB, orders the queue largest item first and
+ * copies the descriptors to device memory it allocates (freed by
+ * lift_batch_destroy).  Needs lift_init; call it outside stream capture.
+ * lift_batch_run launches, on `stream`, a CUDA graph (captured on its first
+ * call) made of a memset node that resets the queue head and the per-op
+ * counters and the persistent kernel; the results are written when the
+ * stream reaches the end of the graph.  Runs of one batch must not overlap.
+ * Reduction results are the FP64 sum, rounded once, of per-item fp32
+ * partials taken in item order, so they do not depend on scheduling.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int op;
+  int variant;
+  int64_t n, M, N, lda;
+  float alpha, beta;
+  const float* x;
+  const float* y;
+  const float* A;
+  float* out;
+} lift_op_desc;
+
+typedef struct lift_batch lift_batch;
+
+lift_status lift_batch_create(const lift_op_desc* ops, int64_t count, lift_batch** batch);
+lift_status lift_batch_run(lift_batch* batch, void* stream);
+/* Work items, algorithmic bytes of one run, and CTAs of the persistent grid. */
+lift_status lift_batch_info(const lift_batch* batch, int64_t* items, int64_t* bytes, int64_t* grid);
+/* For op i: the variant the batch adopted, the processing mode it maps to
+ * (vector ops: 0..5 = (vector width, vectors per thread per tile) of
+ * (1,4) (4,1) (4,2) (4,4) (8,1) (8,2), tile = 256 threads x both; gemv:
+ * 0..2 = vector width 1, 4, 8), and the work-item length in elements
+ * (gemv: rows).  Any output pointer may be NULL. */
+lift_status lift_batch_op_choice(const lift_batch* batch, int64_t i, int* variant, int* mode,
+                                 int64_t* item);
+/* Synchronises the device, then frees the batch's device memory. */
+lift_status lift_batch_destroy(lift_batch* batch);
+
+/* ------------------------------------------------------------------------
  * Cost-model training kernels (FP32).  A multilayer perceptron
  * d_in -> h1 -> h2 -> V (ReLU hidden layers) predicts one log-time per
  * kernel variant from the features of a call (lift_features); it replaces

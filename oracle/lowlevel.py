@@ -136,6 +136,37 @@ def final_combine(P: int, ft: int, cast32: bool = True):
     return C(Join(), MapWorkgroup(body), Split(P))
 
 
+def cta_expr(op: str, K: int, tile: int, vw: int, threads: int, stride: bool = True):
+    """One CTA folding K tiles of ``tile`` elements (in order) into one
+    value: per-thread folds over vect^vw lanes, lane sum, block tree."""
+    V = tile // vw
+    J = V // threads
+    assert V % threads == 0 and tile % vw == 0
+    f = absAndPlus if op == "asum" else fold(add, mult)
+    fr = Vect(vw, f) if vw > 1 else f
+    lanes = Id()
+    if vw > 1:
+        lanes = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
+    return C(block_tree(threads), lanes, Join(), MapLocal(ReduceSeq(fr, 0)),
+             _thread_order(threads, K * J, J, stride),
+             AsVector(vw) if vw > 1 else Id())
+
+
+def batch_reduce(op: str, n: int, item: int, tile: int, vw: int, threads: int = 256,
+                 ft: int = 256, cast32: bool = True):
+    """One asum/dot op of the batched launch: split^item into work items,
+    each folded by one CTA like a kernel tile sequence (cta_expr), then
+    the FP64 combine of the item partials in item order."""
+    P = max(1, math.ceil(n / item))
+    K = item // tile
+    L = P * item
+    e = C(final_combine(P, ft, cast32), Join(), MapWorkgroup(cta_expr(op, K, tile, vw, threads)),
+          Split(item), PadTo(L))
+    if op == "dot":
+        e = C(e, Zip())
+    return e, L
+
+
 def reduce_variant(op: str, n: int, tile: int, vw: int, threads: int, grid: int,
                    stride: bool = True, cluster: int = 1, ft: int = 256,
                    cast32: bool = True):
@@ -157,15 +188,7 @@ def reduce_variant(op: str, n: int, tile: int, vw: int, threads: int, grid: int,
     V = tile // vw
     J = V // threads
     assert V % threads == 0 and tile % vw == 0 and grid % cluster == 0
-    f = absAndPlus if op == "asum" else fold(add, mult)
-    fr = Vect(vw, f) if vw > 1 else f
-    per_thread = K * J
-    lanes = Id()
-    if vw > 1:
-        lanes = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
-    cta = C(block_tree(threads), lanes, Join(), MapLocal(ReduceSeq(fr, 0)),
-            _thread_order(threads, per_thread, J, stride),
-            AsVector(vw) if vw > 1 else Id())
+    cta = cta_expr(op, K, tile, vw, threads, stride)
     parts = C(Join(), MapWorkgroup(cta), Split(K * tile), Join(),
               ReorderStride(s=grid), Split(tile), PadTo(L))
     P = grid

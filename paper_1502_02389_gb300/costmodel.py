@@ -17,14 +17,17 @@ only arranges the data and calls them.
 from __future__ import annotations
 
 import math
+import os
 from collections import defaultdict
 from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
-from . import lift
+from . import lift, tune
 
 D_IN, H1, H2 = 10, 64, 64
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+WEIGHTS = os.path.join(DATA, "mlp_gb300.txt")   # trained on the GB300 sweep
 
 
 def offsets() -> Tuple[List[int], int]:
@@ -183,3 +186,51 @@ def best_fixed(records: List[Dict]) -> Dict[int, int]:
                 score.append((np.mean([math.log(t[v] / min(t.values())) for t in rows]), v))
         best[op] = min(score)[1]
     return best
+
+
+def evaluate_policies(train: List[Dict], heldout: List[Dict], weights: str, table: str):
+    """Regret on the held-out sweep of the learned pick (MLP policy through
+    lift_pick) and of the two methods without the model: the single best
+    fixed variant per op and the nearest-shape tuned table."""
+    res = {}
+    lift.lift_set_policy(lift.POLICY_MLP, weights)
+    try:
+        res["mlp"] = summary(regrets(heldout, lambda op, n, M, N: lift.lift_pick(op, n, M, N)))
+    finally:
+        lift.lift_set_policy(lift.POLICY_FIXED)
+    bf = best_fixed(train)
+    res["best_fixed"] = summary(regrets(heldout, lambda op, n, M, N: bf[op]))
+    tune.write_table(train, table)
+    lift.lift_set_policy(lift.POLICY_TABLE, table)
+    try:
+        res["table"] = summary(regrets(heldout, lambda op, n, M, N: lift.lift_pick(op, n, M, N)))
+    finally:
+        lift.lift_set_policy(lift.POLICY_FIXED)
+    return res
+
+
+def main():
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="train the variant cost model on the GPU")
+    ap.add_argument("--train", default=os.path.join(DATA, "timings_gb300_train.csv"))
+    ap.add_argument("--heldout", default=os.path.join(DATA, "timings_gb300_heldout.csv"))
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    lift.lift_init()
+    tr, ho = tune.load_csv(a.train), tune.load_csv(a.heldout)
+    _, X, T, M = dataset(tr)
+    trainer = Trainer(X, T, M, seed=a.seed)
+    hist = trainer.train(a.steps, a.lr, log_every=max(1, a.steps // 10))
+    save(a.out, trainer.params(), T.shape[1])
+    res = evaluate_policies(tr, ho, a.out, a.out + ".table")
+    res.update({"loss": hist, "train_timings": len(tr), "heldout_timings": len(ho),
+                "train_shapes": int(X.shape[0])})
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -31,6 +31,14 @@ class LiftError(RuntimeError):
         super().__init__(f"{where}: status {status} ({status_string(status)}) {detail}".strip())
 
 
+class OpDesc(ctypes.Structure):
+    """lift_op_desc"""
+    _fields_ = [("op", ctypes.c_int), ("variant", ctypes.c_int), ("n", ctypes.c_int64),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("A", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
 class VariantInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in ("op", "id", "tile", "vw", "threads", "stride", "tree",
                                            "cluster", "passes", "stages", "rows", "lanes",
@@ -67,6 +75,13 @@ _SIGS = {
     "lift_pick": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lift_features": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "lift_asum_noalloc": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_batch_create": ([ctypes.c_void_p, _I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "lift_batch_run": ([_P, _P], ctypes.c_int),
+    "lift_batch_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+                        ctypes.c_int),
+    "lift_batch_op_choice": ([_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(_I64)], ctypes.c_int),
+    "lift_batch_destroy": ([_P], ctypes.c_int),
     "lift_mlp_param_count": ([ctypes.c_int] * 4, _I64),
     "lift_mlp_work_count": ([_I64, ctypes.c_int, ctypes.c_int], _I64),
     "lift_mlp_forward": ([ctypes.c_int] * 4 + [_P, _P, _I64, _P, _P, _P], ctypes.c_int),
@@ -244,6 +259,44 @@ def lift_features(op: int, n: int, M: int = 0, N: int = 0) -> List[float]:
 
 def lift_asum_noalloc(x, n, result, stream=None):
     _check(lib().lift_asum_noalloc(_ptr(x), n, _ptr(result), _stream(stream)), "lift_asum_noalloc")
+
+
+def lift_batch_create(descs) -> int:
+    """descs: a ctypes array of OpDesc (or a list of dicts with its fields);
+    returns the opaque batch handle."""
+    if not isinstance(descs, ctypes.Array):
+        arr = (OpDesc * len(descs))()
+        for i, d in enumerate(descs):
+            for k, v in d.items():
+                setattr(arr[i], k, _ptr(v) if k in ("x", "y", "A", "out") else v)
+        descs = arr
+    h = ctypes.c_void_p()
+    _check(lib().lift_batch_create(ctypes.cast(descs, ctypes.c_void_p), len(descs), ctypes.byref(h)),
+           "lift_batch_create")
+    return h.value
+
+
+def lift_batch_run(batch, stream=None):
+    _check(lib().lift_batch_run(batch, _stream(stream)), "lift_batch_run")
+
+
+def lift_batch_info(batch):
+    it, by, gr = _I64(), _I64(), _I64()
+    _check(lib().lift_batch_info(batch, ctypes.byref(it), ctypes.byref(by), ctypes.byref(gr)),
+           "lift_batch_info")
+    return {"items": it.value, "bytes": by.value, "grid": gr.value}
+
+
+def lift_batch_op_choice(batch, i):
+    """(variant, mode, item length) of op i."""
+    v, m, it = ctypes.c_int(), ctypes.c_int(), _I64()
+    _check(lib().lift_batch_op_choice(batch, i, ctypes.byref(v), ctypes.byref(m), ctypes.byref(it)),
+           "lift_batch_op_choice")
+    return v.value, m.value, it.value
+
+
+def lift_batch_destroy(batch):
+    _check(lib().lift_batch_destroy(batch), "lift_batch_destroy")
 
 
 def lift_mlp_param_count(d_in, h1, h2, V) -> int:

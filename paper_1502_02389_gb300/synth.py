@@ -15,6 +15,13 @@ GB300):
   mixed          n = 2^28, N(0, 1) with 1 % of entries scaled by 1e3,
                  stored as bf16 or as fp8-e4m3 with one fp32 scale per 4096
                  consecutive elements, seed 4
+  batch          20,000 ops, op uniform over {asum, dot, gemv}, vector
+                 lengths round(2^U(8, 22)), gemv M, N = round(2^U(6, 12))
+                 independently (PCG64 seed 3); every array a disjoint,
+                 256-byte aligned slice of one pool (about 60 GB) whose values
+                 are N(0, 1), drawn on the device by torch's generator seeded
+                 3 (drawing 15 G values on the host would take minutes); gemv
+                 alpha = 1, beta = 0.5
 """
 from __future__ import annotations
 
@@ -116,3 +123,55 @@ def encode_fp8_blocks(v, block: int = FP8_BLOCK):
     blk = np.arange(v.size) // block
     q = encode_e4m3(v / s[blk].astype(np.float64))
     return q, s
+
+
+# ---------------------------------------------------------------------------
+# batched workload
+# ---------------------------------------------------------------------------
+ASUM, DOT, GEMV = 0, 1, 3   # op ids of the library's C-ABI
+
+
+def batch_ops(count: int = 20000, seed: int = 3, lo: float = 8, hi: float = 22,
+              mlo: float = 6, mhi: float = 12):
+    """Op types and sizes of the batched workload."""
+    g = generator(seed)
+    kind = g.integers(0, 3, count)
+    n = np.rint(2.0 ** g.uniform(lo, hi, count)).astype(np.int64)
+    M = np.rint(2.0 ** g.uniform(mlo, mhi, count)).astype(np.int64)
+    N = np.rint(2.0 ** g.uniform(mlo, mhi, count)).astype(np.int64)
+    ops = []
+    for i in range(count):
+        op = (ASUM, DOT, GEMV)[int(kind[i])]
+        if op == GEMV:
+            ops.append({"op": op, "n": 0, "M": int(M[i]), "N": int(N[i])})
+        else:
+            ops.append({"op": op, "n": int(n[i]), "M": 0, "N": 0})
+    return ops
+
+
+def batch_layout(ops, align_elems: int = 64):
+    """Disjoint, 256-byte aligned element offsets into one fp32 pool:
+    per op {'x', 'y', 'A', 'out'} (absent arrays omitted); returns the
+    offsets and the pool length in elements."""
+    off = 0
+    lay = []
+
+    def take(count):
+        nonlocal off
+        o = off
+        off += (max(count, 1) + align_elems - 1) // align_elems * align_elems
+        return o
+
+    for d in ops:
+        e = {}
+        if d["op"] == GEMV:
+            e["A"] = take(d["M"] * d["N"])
+            e["x"] = take(d["N"])
+            e["out"] = take(d["M"])
+        else:
+            e["x"] = take(d["n"])
+            if d["op"] == DOT:
+                e["y"] = take(d["n"])
+            e["out"] = take(1)
+        lay.append(e)
+    return lay, off

@@ -234,6 +234,29 @@ def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], r
     return out
 
 
+CSV_HEADER = "device,op,n,M,N,variant,ms"
+
+
+def export_csv(records: List[Dict], path: str) -> None:
+    """Compact copy of a timing database (one line per measurement)."""
+    with open(path, "w") as f:
+        f.write(CSV_HEADER + "\n")
+        for r in records:
+            f.write(f"{r['device']},{r['op']},{r['n']},{r['M']},{r['N']},{r['variant']},{r['ms']:.6g}\n")
+
+
+def load_csv(path: str) -> List[Dict]:
+    out = []
+    with open(path) as f:
+        head = f.readline().strip()
+        assert head == CSV_HEADER, head
+        for line in f:
+            d, op, n, M, N, v, ms = line.strip().split(",")
+            out.append({"device": d, "op": int(op), "n": int(n), "M": int(M), "N": int(N),
+                        "variant": int(v), "ms": float(ms)})
+    return out
+
+
 def best_per_shape(records: List[Dict]) -> Dict[Tuple, Dict]:
     best: Dict[Tuple, Dict] = {}
     for r in records:
@@ -294,6 +317,7 @@ def main():
     ap.add_argument("--seed", type=int, default=11)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--table", default=None)
+    ap.add_argument("--csv", default=None)
     ap.add_argument("-v", action="store_true")
     a = ap.parse_args()
     if a.preset == "workloads":
@@ -303,6 +327,8 @@ def main():
     sweep(shapes, a.db, reps=a.reps, verbose=a.v)
     if a.table:
         write_table(load_db(a.db), a.table)
+    if a.csv:
+        export_csv(load_db(a.db), a.csv)
 
 
 if __name__ == "__main__":

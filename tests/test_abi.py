@@ -93,3 +93,24 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     with pytest.raises(lift.LiftError) as e:
         lift.lift_asum_ex(lift.BF16, 4096, 8192, 10, 64, None, 0)  # bf16 takes no scales
     assert e.value.status == lift.ERR_INVALID_ARG
+
+
+def test_batch_create_rejects_bad_descriptors_before_any_device_work(lib):
+    from paper_1502_02389_gb300 import lift
+    good = {"op": lift.OP_ASUM, "variant": -1, "n": 10, "x": 4096, "out": 8192}
+    bad = [
+        dict(good, op=lift.OP_ASUM_FP8),            # op id not supported by the batch
+        dict(good, op=99),                           # op id out of range
+        dict(good, variant=10 ** 5),                 # variant id out of range
+        dict(good, n=-1),
+        dict(good, x=0),                             # NULL x with n > 0
+        dict(good, out=0),
+        dict(good, x=4098),                          # not 4-byte aligned
+        {"op": lift.OP_GEMV, "variant": -1, "M": 4, "N": 8, "lda": 7, "x": 64, "A": 128, "out": 256},
+        {"op": lift.OP_DOT, "variant": -1, "n": 5, "x": 64, "y": 0, "out": 256},
+    ]
+    for d in bad:
+        with pytest.raises(lift.LiftError) as e:
+            lift.lift_batch_create([good, d])
+        assert e.value.status == lift.ERR_INVALID_ARG, d
+        assert "batch op 1" in lift.lib().lift_last_error().decode()

@@ -260,3 +260,18 @@ def test_gemv_variant_expression_exact(N, vw):
     x = rng.integers(-9, 9, N).astype(float)
     z = evaluate(ll.gemv_z_variant(M, N, 2.0, vw, 32, 2), A, env={"x": x})
     assert np.array_equal(z, 2.0 * (A @ x))
+
+
+@pytest.mark.parametrize("n,item,tile,vw", [(0, 1024, 1024, 1), (1, 2048, 1024, 4),
+                                            (5000, 2048, 1024, 4), (70001, 8192, 4096, 8)])
+def test_batch_expression_exact_on_integers(n, item, tile, vw):
+    rng = np.random.default_rng(n + 1)
+    x = rng.integers(-500, 500, n).astype(float)
+    y = rng.integers(-9, 9, n).astype(float)
+    # cast32=False: the FP64 combine before the final rounding to fp32
+    e, Lp = ll.batch_reduce("asum", n, item, tile, vw, cast32=False)
+    xp = np.concatenate([x, np.zeros(Lp - n)])
+    assert evaluate(e, xp)[0] == np.abs(x).sum()
+    e, Lp = ll.batch_reduce("dot", n, item, tile, vw, cast32=False)
+    yp = np.concatenate([y, np.zeros(Lp - n)])
+    assert evaluate(e, (xp, yp))[0] == x @ y
