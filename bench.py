@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "dot_scal": dict(n=1 << 26, desc="dot(x,y) + scal(1.5,x) fp32, n=2^26, N(0,1) seed 1"),
     "asum": dict(n=1 << 20, desc="asum(x) fp32, n=2^20, U(-1,1) seed 0, L2 flushed per step"),
+    "asum_large": dict(n=1 << 26, desc="asum(x) fp32, n=2^26, N(0,1) seed 1"),
+    "mixed": dict(n=1 << 28, desc="asum and dot on bf16 and on fp8-e4m3 (+ per-4096 scales), "
+                                  "n=2^28, N(0,1) with 1% x1e3, seed 4"),
     "gemv_square": dict(M=8192, N=8192, desc="gemv fp32 8192x8192, alpha=1, beta=0.5, seed 2"),
     "gemv_tall": dict(M=65536, N=1024, desc="gemv fp32 65536x1024, alpha=1, beta=0.5, seed 2"),
     "batch": dict(desc="batched launch: 20,000 ops (asum/dot/gemv, lengths 2^U(8,22), "
@@ -52,13 +55,13 @@ def peaks():
 
 
 KERNEL_SOURCE = {"asum": "reduce_f32.cu", "dot": "reduce_f32.cu", "scal": "scal_gemv.cu",
-                 "gemv": "scal_gemv.cu", "batch": "batch.cu"}
+                 "gemv": "scal_gemv.cu", "batch": "batch.cu", "mixed": "mixed.cu"}
 
 
 def kernel_hash(tag: str) -> str:
     """Hash of the source of the kernel a tag names (its .cu file and the
     shared device header): ncu counters taken on other sources are stale."""
-    op = tag.split("_", 1)[0]
+    op = "mixed" if ("bf16" in tag or "fp8" in tag) else tag.split("_", 1)[0]
     d = os.path.join(ROOT, "paper_1502_02389_gb300", "csrc")
     h = hashlib.sha256()
     for f in (KERNEL_SOURCE.get(op, ""), "lift_internal.cuh"):
@@ -81,6 +84,22 @@ def traffic_for(kernel_tag: str):
         if len(f) == 3 and f[0] == kernel_tag and f[1] == want:
             return float(f[2])
     return None
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (replicas: every rank runs its own copy of the
+    step; the job is as fast as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(bytes_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job GB/s: the bytes all ranks moved over the slowest rank's time."""
+    return world * bytes_per_rank_step * steps / (max_ms / 1e3) / 1e9
 
 
 class Clocks:
@@ -195,6 +214,68 @@ def run_ours(args, rank, world, dist):
         h2d, d2h = 8 * n, 4 * n + 4
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pd["name"], ps["name"]],
                   "l2": "no flush: inputs 3 x 256 MiB exceed the 129 MB L2"}
+    elif wl == "mixed":
+        n = WORKLOADS[wl]["n"]
+        xv, yv = synth.mixed_values(n)
+        bx, by = synth.encode_bf16(xv), synth.encode_bf16(yv)
+        (qx, sx), (qy, sy) = synth.encode_fp8_blocks(xv), synth.encode_fp8_blocks(yv)
+        del xv, yv
+        t = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
+        bxd, byd, qxd, qyd, sxd, syd = t(bx), t(by), t(qx), t(qy), t(sx), t(sy)
+        r = torch.zeros(4, device=dev)
+        calls = []
+        for name, op, dt, args, nb in (
+                ("asum_bf16", lift.OP_ASUM_BF16, lift.BF16, (bxd, None), 2 * n),
+                ("dot_bf16", lift.OP_DOT_BF16, lift.BF16, (bxd, None, byd, None), 4 * n),
+                ("asum_fp8", lift.OP_ASUM_FP8, lift.FP8_E4M3, (qxd, sxd), n + 4 * sx.size),
+                ("dot_fp8", lift.OP_DOT_FP8, lift.FP8_E4M3, (qxd, sxd, qyd, syd),
+                 2 * n + 8 * sx.size)):
+            v = lift.lift_pick(op, n)
+            calls.append((op, dt, args, v, lift.lift_variant_describe(op, v)["name"], nb))
+        kernels = [["mixed:" + name, nb, [], []] for (_, _, _, _, name, nb) in calls]
+        bytes_step = sum(c[5] for c in calls)
+        launches_per_step = 4
+
+        def step(timed):
+            for i, (op, dt, args, v, name, nb) in enumerate(calls):
+                if timed:
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(s)
+                if len(args) == 2:
+                    lift.lift_asum_ex_v(v, dt, args[0], args[1], n, r[i:i + 1])
+                else:
+                    lift.lift_dot_ex_v(v, dt, args[0], args[1], args[2], args[3], n, r[i:i + 1])
+                if timed:
+                    b.record(s)
+                    kernels[i][2].append(a); kernels[i][3].append(b)
+
+        e2e_step, host, h2d, d2h = None, {}, 0, 0
+        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [c[4] for c in calls],
+                  "l2": "no flush: every input is at least 256 MiB"}
+    elif wl == "asum_large":
+        n = WORKLOADS[wl]["n"]
+        xh, _, _ = synth.dot_scal(n)
+        x = torch.from_numpy(xh).to(dev)
+        r = torch.zeros(1, device=dev)
+        va = lift.lift_pick(lift.OP_ASUM, n)
+        pa = lift.lift_variant_describe(lift.OP_ASUM, va)
+        launches_per_step = pa["passes"]
+        bytes_step = 4 * n
+        kas = ["asum:" + pa["name"], 4 * n, [], []]
+        kernels = [kas]
+
+        def step(timed):
+            if timed:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(s)
+            lift.lift_asum_v(va, x, n, r)
+            if timed:
+                ev[1].record(s)
+                kas[2].append(ev[0]); kas[3].append(ev[1])
+
+        e2e_step, host, h2d, d2h = None, {}, 0, 0
+        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
+                  "l2": "no flush: x is 256 MiB, larger than the 129 MB L2"}
     elif wl == "asum":
         n = WORKLOADS[wl]["n"]
         xh = synth.asum_small(n)
@@ -229,7 +310,7 @@ def run_ours(args, rank, world, dist):
                   "l2": "flushed before every step (a 512 MiB read, outside the kernel events)"}
     elif wl == "batch":
         from paper_1502_02389_gb300 import costmodel
-        ops = synth.batch_ops()
+        ops = synth.batch_ops()[:args.batch_ops]
         lay, total = synth.batch_layout(ops)
         g = torch.Generator(device=dev)
         g.manual_seed(3)
@@ -266,7 +347,7 @@ def run_ours(args, rank, world, dist):
         info = lift.lift_batch_info(hb)
         bytes_step = info["bytes"]
         launches_per_step = 1
-        kb = ["batch:" + main_policy, bytes_step, [], []]
+        kb = ["batch:batch_" + main_policy, bytes_step, [], []]
         kernels = [kb]
 
         def step(timed):
@@ -347,12 +428,9 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     clk = clocks.stop() if clocks else None
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
-    value = world * bytes_step * args.steps / (ms / 1e3) / 1e9
+    value = job_rate(bytes_step, args.steps, world, ms)
 
     # ---- per-kernel durations (events on the launching stream)
     per_kernel = {}
@@ -382,10 +460,7 @@ def run_ours(args, rank, world, dist):
         e1.record(s)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / ek
-        if dist:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(ems, dist, dev)
         e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
     if wl == "batch":
@@ -414,6 +489,21 @@ def oracle_sample(workload: str, budget_s: float):
         x, y, alpha = synth.dot_scal(n)
         work = lambda: (blas.dot(x, y), blas.scal(float(alpha), x))  # noqa: E731
         bytes_one, what = 16 * n, f"full step (dot + scal, n=2^26)"
+    elif workload == "asum_large":
+        n = WORKLOADS[workload]["n"]
+        x, _, _ = synth.dot_scal(n)
+        work = lambda: blas.asum(x)  # noqa: E731
+        bytes_one, what = 4 * n, "full step (asum, n=2^26)"
+    elif workload == "mixed":
+        from oracle import mixed
+        n = 1 << 22
+        xv, yv = synth.mixed_values(n)
+        bx, by = synth.encode_bf16(xv), synth.encode_bf16(yv)
+        (qx, sx), (qy, sy) = synth.encode_fp8_blocks(xv), synth.encode_fp8_blocks(yv)
+        work = lambda: (mixed.asum("bf16", bx), mixed.dot("bf16", bx, None, by, None),  # noqa: E731
+                        mixed.asum("fp8", qx, sx), mixed.dot("fp8", qx, sx, qy, sy))
+        bytes_one = 2 * n + 4 * n + (n + 4 * sx.size) + (2 * n + 8 * sx.size)
+        what = "the four mixed ops on the first 2^22 elements (same recipe, seed 4)"
     elif workload == "asum":
         n = WORKLOADS[workload]["n"]
         x = synth.asum_small(n)
@@ -485,6 +575,8 @@ def main():
     ap.add_argument("--workload", default="dot_scal", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mlp", default=None, help="cost-model weights for the batch workload")
+    ap.add_argument("--batch-ops", type=int, default=20000,
+                    help="ops of the batch workload (fewer only for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
