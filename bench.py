@@ -224,27 +224,27 @@ def run_ours(args, rank, world, dist):
         bxd, byd, qxd, qyd, sxd, syd = t(bx), t(by), t(qx), t(qy), t(sx), t(sy)
         r = torch.zeros(4, device=dev)
         calls = []
-        for name, op, dt, args, nb in (
+        for name, op, dt, dargs, nb in (
                 ("asum_bf16", lift.OP_ASUM_BF16, lift.BF16, (bxd, None), 2 * n),
                 ("dot_bf16", lift.OP_DOT_BF16, lift.BF16, (bxd, None, byd, None), 4 * n),
                 ("asum_fp8", lift.OP_ASUM_FP8, lift.FP8_E4M3, (qxd, sxd), n + 4 * sx.size),
                 ("dot_fp8", lift.OP_DOT_FP8, lift.FP8_E4M3, (qxd, sxd, qyd, syd),
                  2 * n + 8 * sx.size)):
             v = lift.lift_pick(op, n)
-            calls.append((op, dt, args, v, lift.lift_variant_describe(op, v)["name"], nb))
+            calls.append((op, dt, dargs, v, lift.lift_variant_describe(op, v)["name"], nb))
         kernels = [["mixed:" + name, nb, [], []] for (_, _, _, _, name, nb) in calls]
         bytes_step = sum(c[5] for c in calls)
         launches_per_step = 4
 
         def step(timed):
-            for i, (op, dt, args, v, name, nb) in enumerate(calls):
+            for i, (op, dt, da, v, name, nb) in enumerate(calls):
                 if timed:
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record(s)
-                if len(args) == 2:
-                    lift.lift_asum_ex_v(v, dt, args[0], args[1], n, r[i:i + 1])
+                if len(da) == 2:
+                    lift.lift_asum_ex_v(v, dt, da[0], da[1], n, r[i:i + 1])
                 else:
-                    lift.lift_dot_ex_v(v, dt, args[0], args[1], args[2], args[3], n, r[i:i + 1])
+                    lift.lift_dot_ex_v(v, dt, da[0], da[1], da[2], da[3], n, r[i:i + 1])
                 if timed:
                     b.record(s)
                     kernels[i][2].append(a); kernels[i][3].append(b)
@@ -463,6 +463,22 @@ def run_ours(args, rank, world, dist):
         ems = max_over_ranks(ems, dist, dev)
         e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
+    if wl == "dot_scal":
+        # context: the same step submitted as one 2-op batched launch
+        hb2 = lift.lift_batch_create([
+            {"op": lift.OP_DOT, "variant": -1, "n": n, "x": x, "y": y, "out": r},
+            {"op": lift.OP_SCAL, "variant": -1, "n": n, "alpha": float(alpha), "x": x, "out": z}])
+        for _ in range(3):
+            lift.lift_batch_run(hb2)
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(s)
+        for _ in range(50):
+            lift.lift_batch_run(hb2)
+        b2.record(s)
+        torch.cuda.synchronize()
+        config["same_step_as_one_batched_launch_gbs"] = round(
+            bytes_step * 50 / (a2.elapsed_time(b2) / 1e3) / 1e9, 1)
+        lift.lift_batch_destroy(hb2)
     if wl == "batch":
         config["policies_gbs"] = policy_rates()
         for h in handles.values():

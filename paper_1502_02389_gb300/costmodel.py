@@ -30,12 +30,19 @@ DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 WEIGHTS = os.path.join(DATA, "mlp_gb300.txt")   # trained on the GB300 sweep
 
 
-def offsets() -> Tuple[List[int], int]:
-    """Output index of each op's variant 0, and the total output width V."""
+def offsets(records: Optional[List[Dict]] = None) -> Tuple[List[int], int]:
+    """Output index of each op's variant 0, and the total output width V.
+    With training records, an op's slice covers the variants measured there
+    (a variant added to the library later stays out of the model's picks
+    until the model is retrained); otherwise the library's current lists."""
     off, v = [], 0
     for op in range(lift.NUM_OPS):
         off.append(v)
-        v += lift.lift_variant_count(op)
+        if records is None:
+            v += lift.lift_variant_count(op)
+        else:
+            ids = [r["variant"] for r in records if r["op"] == op]
+            v += (max(ids) + 1) if ids else 0
     return off, v
 
 
@@ -48,8 +55,9 @@ def group(records: List[Dict]) -> Dict[Tuple[int, int, int, int], Dict[int, floa
 
 
 def dataset(records: List[Dict]):
-    """Features X [B, 10], targets T [B, V] = log(t_v / t_best), mask M."""
-    off, V = offsets()
+    """Features X [B, 10], targets T [B, V] = log(t_v / t_best), mask M
+    (the output slices follow ``offsets(records)``)."""
+    off, V = offsets(records)
     g = group(records)
     keys = sorted(g)
     X = np.zeros((len(keys), D_IN), np.float32)
@@ -144,9 +152,11 @@ class Trainer:
         return self.p.cpu().numpy()
 
 
-def save(path: str, params: np.ndarray, V: int) -> None:
-    """Weights file read by lift_set_policy(LIFT_POLICY_MLP, path)."""
-    off, _ = offsets()
+def save(path: str, params: np.ndarray, V: int, off: Optional[List[int]] = None) -> None:
+    """Weights file read by lift_set_policy(LIFT_POLICY_MLP, path); ``off``
+    are the output slices of the training data (``offsets(records)``)."""
+    if off is None:
+        off, _ = offsets()
     with open(path, "w") as f:
         f.write(f"lift-mlp 1 {D_IN} {H1} {H2} {V}\n")
         f.write("offsets " + " ".join(str(o) for o in off) + "\n")
@@ -225,7 +235,7 @@ def main():
     _, X, T, M = dataset(tr)
     trainer = Trainer(X, T, M, seed=a.seed)
     hist = trainer.train(a.steps, a.lr, log_every=max(1, a.steps // 10))
-    save(a.out, trainer.params(), T.shape[1])
+    save(a.out, trainer.params(), T.shape[1], offsets(tr)[0])
     res = evaluate_policies(tr, ho, a.out, a.out + ".table")
     res.update({"loss": hist, "train_timings": len(tr), "heldout_timings": len(ho),
                 "train_shapes": int(X.shape[0])})

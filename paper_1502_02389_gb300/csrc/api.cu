@@ -90,6 +90,8 @@ static lift_status init_device(int device) {
 // ---------------------------------------------------------------------------
 // registry
 // ---------------------------------------------------------------------------
+void register_gemv_tma(std::vector<Variant>& gemv);   // gemv_tma.cu
+
 static std::vector<Variant> g_ops[LIFT_NUM_OPS];
 static std::once_flag g_reg_once;
 
@@ -97,6 +99,7 @@ static void build_registry() {
   register_reduce_f32(g_ops[LIFT_OP_ASUM], g_ops[LIFT_OP_DOT]);
   register_scal(g_ops[LIFT_OP_SCAL]);
   register_gemv(g_ops[LIFT_OP_GEMV]);
+  register_gemv_tma(g_ops[LIFT_OP_GEMV]);
   register_mixed(g_ops);
 }
 
@@ -227,7 +230,10 @@ static int mlp_pick(int op, int64_t n, int64_t M, int64_t N) {
     for (int i = 0; i < m.h1; ++i) s += h1[i] * m.W2[i * m.h2 + j];
     h2[j] = s > 0.f ? s : 0.f;
   }
-  const int cnt = (int)registry(op).size();
+  // variants the weights know: the file's slice of this op (a registry that
+  // grew after training keeps its newer variants out of the pick)
+  const int file_cnt = (op + 1 < LIFT_NUM_OPS ? m.offsets[op + 1] : m.V) - m.offsets[op];
+  const int cnt = std::min((int)registry(op).size(), file_cnt);
   int best = 0;
   float best_t = INFINITY;
   for (int v = 0; v < cnt; ++v) {
@@ -284,6 +290,8 @@ static lift_status resolve(int op, int variant, const Args& a, const Variant** o
   const int al = v->align_bytes;
   bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
   if (op == LIFT_OP_GEMV) ok = ok && ((a.lda * 4) % al == 0);
+  // bulk copies move whole 16-byte granules of each row
+  if (op == LIFT_OP_GEMV && v->info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
   if (!ok && v->fallback >= 0) v = &L[v->fallback];
   *out = v;
   return LIFT_OK;

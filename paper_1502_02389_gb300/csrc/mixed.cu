@@ -14,8 +14,8 @@
 //    the product of two bf16 or two e4m3 values is exact in fp32;
 //  * each thread takes E = 4096/THREADS consecutive elements of a block
 //    (coalesced 16/32-byte loads) and sums its E terms with a halving tree
-//    (pairwise, depth log2 E; for fp8 asum this sum is exact: E <= 32 values
-//    on the 2^-9 grid below 2^14 need at most 23 bits);
+//    (pairwise, depth log2 E; for fp8 asum this sum is exact: E <= 64 values
+//    on the 2^-9 grid below 2^15 need at most 24 bits);
 //  * the block sum is multiplied once by the block scale (fp8: s_x, or
 //    s_x * s_y for dot) and added into a (sum, compensation) pair with
 //    Knuth's TwoSum;
@@ -288,10 +288,13 @@ struct Mixed {
   static const void* kernel() {
     return reinterpret_cast<const void*>(&mixed_reduce<OP, DT, THREADS, U, GUARDED>);
   }
+  // persistent grid with the same number of blocks for every CTA
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t nb = a.n > 0 ? (a.n + kBlock - 1) / kBlock : 1;
-    int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
-    return g < nb ? g : nb;
+    const int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
+    if (g <= 0) return 0;
+    const int64_t per = (nb + g - 1) / g;
+    return (nb + per - 1) / per;
   }
   static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
     DeviceState* st = current_state();
@@ -350,6 +353,12 @@ void register_one(std::vector<Variant>& L, int opid, const char* tag) {
   snprintf(nm, sizeof nm, "%s_t256_guarded", tag);
   L.push_back(mixed_variant<OP, DT, 256, 1, true>(opid, nm));
   const int guarded = static_cast<int>(L.size()) - 1;
+  // 64 elements per thread per block: the block's decode, scale and
+  // compensation work is spread over more elements
+  snprintf(nm, sizeof nm, "%s_t64_u2", tag);
+  L.push_back(mixed_variant<OP, DT, 64, 2, false>(opid, nm));
+  snprintf(nm, sizeof nm, "%s_t64_u4", tag);
+  L.push_back(mixed_variant<OP, DT, 64, 4, false>(opid, nm));
   for (size_t i = 0; i < L.size(); ++i) {
     L[i].info.id = static_cast<int>(i);
     L[i].fallback = guarded;

@@ -269,11 +269,14 @@ struct ReduceF32 {
   }
   static size_t smem() { return (size_t)STAGES * NIN * TILE * sizeof(float); }
 
+  // Persistent grid, shrunk so that every CTA takes the same number of tiles
+  // (ceil(T / G_max) each): no CTA runs a last tile alone.
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t T = a.n > 0 ? (a.n + TILE - 1) / TILE : 1;
     int64_t g = persistent_grid(kernel(), THREADS, smem(), CLUSTER);
     if (g <= 0) return 0;
-    if (T < g) g = T;
+    const int64_t per = (T + g - 1) / g;
+    g = (T + per - 1) / per;
     g = (g + CLUSTER - 1) / CLUSTER * CLUSTER;
     return g;
   }

@@ -130,10 +130,13 @@ struct Scal {
       return reinterpret_cast<const void*>(&scal_tma<THREADS, TILE, STAGES>);
   }
   static size_t smem() { return (size_t)STAGES * TILE * sizeof(float); }
+  // persistent grid with the same number of tiles for every CTA
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t T = a.n > 0 ? (a.n + TILE - 1) / TILE : 1;
-    int64_t g = persistent_grid(kernel(), THREADS, smem(), 1);
-    return g < T ? g : T;
+    const int64_t g = persistent_grid(kernel(), THREADS, smem(), 1);
+    if (g <= 0) return 0;
+    const int64_t per = (T + g - 1) / g;
+    return (T + per - 1) / per;
   }
   static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
     const int64_t g = grid(v, a);

@@ -57,11 +57,12 @@ MAX_ROT = 64
 
 
 def rotation(nbytes: int) -> int:
-    """Calls in one timed graph: 1 for working sets of at least twice the
-    L2 (they are cold anyway), else enough distinct slices of a 1 GiB pool
-    that a slice is evicted before it is read again."""
+    """Calls in one timed graph: for working sets of at least twice the L2
+    (cold anyway) as many slices of the 1 GiB pool as fit, up to 4 (so the
+    event resolution is shared by several calls), else enough distinct
+    slices that a slice is evicted before it is read again."""
     if nbytes >= 2 * L2_BYTES:
-        return 1
+        return int(max(1, min(4, POOL_BYTES // max(nbytes, 1))))
     return int(max(2, min(MAX_ROT, POOL_BYTES // max(nbytes, 1))))
 
 

@@ -35,7 +35,7 @@ def test_learned_pick_regret_and_gain(L, tmp_path):
     hist = trainer.train(3000, 3e-3, log_every=300)
     assert hist[-1] < 0.5 * hist[0]
     w = str(tmp_path / "mlp.txt")
-    cm.save(w, trainer.params(), T.shape[1])
+    cm.save(w, trainer.params(), T.shape[1], cm.offsets(tr)[0])
     res = cm.evaluate_policies(tr, ho, w, str(tmp_path / "table.txt"))
     print(res)
     assert res["mlp"]["geomean"] <= 1.10

@@ -36,7 +36,7 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("B", [1, 37, 1200])
 def test_forward_loss_and_gradients_match_oracle(L, B):
-    _, V = cm.offsets()
+    _, V = cm.offsets()   # the library's current variant count
     X, T, M = _problem(B, V, B)
     tr = cm.Trainer(X, T, M, seed=3)
     loss, g = tr.grads()
@@ -54,7 +54,7 @@ def test_forward_loss_and_gradients_match_oracle(L, B):
 
 
 def test_adam_steps_match_oracle(L):
-    _, V = cm.offsets()
+    _, V = cm.offsets()   # the library's current variant count
     X, T, M = _problem(64, V, 9)
     tr = cm.Trainer(X, T, M, seed=4)
     p = cm.unflatten(tr.params(), V)
@@ -73,7 +73,7 @@ def test_adam_steps_match_oracle(L):
 
 
 def test_training_fits_a_smooth_target(L):
-    _, V = cm.offsets()
+    _, V = cm.offsets()   # the library's current variant count
     rng = np.random.default_rng(1)
     X = rng.random((800, cm.D_IN)).astype(np.float32)
     W = rng.standard_normal((cm.D_IN, V)).astype(np.float32)

@@ -75,3 +75,19 @@ def test_sweep_writes_and_resumes(L, tmp_path):
     assert all(r["ms"] > 0 and r["gbs"] > 0 for r in recs)
     assert len(tune.sweep(shapes, db, reps=3, warmup=1)) == 0      # resumed: nothing left
     assert len(tune.load_db(db)) == counts
+
+
+def test_committed_cost_model_beats_the_method_without_it(L, tmp_path):
+    """The weights under data/ (trained on the GPU from the committed sweep),
+    loaded by the library's MLP policy, pick variants within 10 % of the
+    exhaustive best on the held-out shapes, better than the best fixed
+    variant per op."""
+    import os
+    from paper_1502_02389_gb300 import costmodel as cm
+    tr = tune.load_csv(os.path.join(cm.DATA, "timings_gb300_train.csv"))
+    ho = tune.load_csv(os.path.join(cm.DATA, "timings_gb300_heldout.csv"))
+    res = cm.evaluate_policies(tr, ho, cm.WEIGHTS, str(tmp_path / "table.txt"))
+    assert res["mlp"]["shapes"] >= 499
+    assert res["mlp"]["geomean"] <= 1.10
+    assert res["mlp"]["geomean"] < res["best_fixed"]["geomean"]
+    assert res["mlp"]["geomean"] < res["table"]["geomean"]
