@@ -2,8 +2,11 @@
 
 Default workload (the dot/scal configuration): fp32 vectors x, y of
 n = 2^26 elements ~ N(0,1) (seed 1), alpha = 1.5.  One step is
-dot(x, y) followed by scal(alpha, x) -> z, each through the C-ABI with the
-policy-picked variant.  The metric is HBM GB/s of algorithmic traffic
+dot(x, y) and scal(alpha, x) -> z with the variants the cost model picks,
+submitted through the C-ABI as one batched persistent launch
+(``--mode batched``, the default) or as two calls (``--mode calls``); the
+other submission is measured too and reported in ``config``, with the
+learned pick's slowdown against an on-the-spot exhaustive sweep of each op.  The metric is HBM GB/s of algorithmic traffic
 (dot reads 8n bytes, scal reads 4n and writes 4n bytes; 16n per step) and
 its fraction of the measured HBM peak.  Inputs (3 x 256 MiB) exceed the
 129 MB L2, so no flush is needed between steps.
@@ -84,6 +87,26 @@ def traffic_for(kernel_tag: str):
         if len(f) == 3 and f[0] == kernel_tag and f[1] == want:
             return float(f[2])
     return None
+
+
+def learned_gap(shapes, picked):
+    """t(picked variant) / t(best variant) for each op of the step, all
+    variants timed on the spot the way the autotuner times them (CUDA graph
+    of back-to-back calls over cold slices, median of 5 replays)."""
+    from paper_1502_02389_gb300 import lift, tune
+    timer, pools = tune.Timer(), tune.Pools(seed=1)
+    out = {}
+    for (op, n, M, N) in shapes:
+        buf = tune.Buffers(pools, op, n, M, N)
+        times = {v: timer.per_call_ms([buf.call(v, r) for r in range(buf.R)], 5, 2)
+                 for v in range(lift.lift_variant_count(op))}
+        best = min(times, key=times.get)
+        out[lift.OP_NAMES[op]] = {
+            "picked": lift.lift_variant_describe(op, picked[op])["name"],
+            "best": lift.lift_variant_describe(op, best)["name"],
+            "ratio": round(times[picked[op]] / times[best], 4)}
+    pools.cache.clear()
+    return out
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -168,6 +191,21 @@ def run_ours(args, rank, world, dist):
     launches_per_step = 0
     kernels = []   # (tag, bytes per launch, start events, end events)
 
+    for name in args.variant or []:          # pin variants by name (profiling)
+        for op in range(lift.NUM_OPS):
+            ids = [v["id"] for v in lift.variants(op) if v["name"] == name]
+            if ids:
+                lift.lift_set_variant(op, ids[0])
+                break
+        else:
+            raise SystemExit(f"unknown variant {name}")
+    policy = "fixed"
+    if wl != "batch" and not args.fixed_policy:
+        from paper_1502_02389_gb300 import costmodel
+        weights = args.mlp or costmodel.WEIGHTS
+        if os.path.exists(weights):
+            lift.lift_set_policy(lift.POLICY_MLP, weights)
+            policy = "mlp"
     if wl == "dot_scal":
         n = WORKLOADS[wl]["n"]
         xh, yh, alpha = synth.dot_scal(n)
@@ -178,33 +216,57 @@ def run_ours(args, rank, world, dist):
         vs = lift.lift_pick(lift.OP_SCAL, n)
         pd = lift.lift_variant_describe(lift.OP_DOT, vd)
         ps = lift.lift_variant_describe(lift.OP_SCAL, vs)
-        launches_per_step = pd["passes"] + 1
         bytes_step = 16 * n
-        kdot = ["dot:" + pd["name"], 8 * n, [], []]
-        kscal = ["scal:" + ps["name"], 8 * n, [], []]
-        kernels = [kdot, kscal]
+        hb2 = lift.lift_batch_create([
+            {"op": lift.OP_DOT, "variant": vd, "n": n, "x": x, "y": y, "out": r},
+            {"op": lift.OP_SCAL, "variant": vs, "n": n, "alpha": float(alpha), "x": x, "out": z}])
 
-        def step(timed):
-            if timed:
-                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ev[0].record(s)
+        def calls():
             lift.lift_dot_v(vd, x, y, n, r)
-            if timed:
-                ev2 = torch.cuda.Event(enable_timing=True)
-                ev[1].record(s)
-                kdot[2].append(ev[0]); kdot[3].append(ev[1])
-                ev2.record(s)
             lift.lift_scal_v(vs, n, float(alpha), x, z)
-            if timed:
-                ev3 = torch.cuda.Event(enable_timing=True)
-                ev3.record(s)
-                kscal[2].append(ev2); kscal[3].append(ev3)
+
+        if args.mode == "batched":
+            launches_per_step = 1
+            kb = ["batch:batch_dot_scal", bytes_step, [], []]
+            kernels = [kb]
+
+            def step(timed):
+                if timed:
+                    ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev[0].record(s)
+                lift.lift_batch_run(hb2)
+                if timed:
+                    ev[1].record(s)
+                    kb[2].append(ev[0]); kb[3].append(ev[1])
+        else:
+            launches_per_step = pd["passes"] + 1
+            kdot = ["dot:" + pd["name"], 8 * n, [], []]
+            kscal = ["scal:" + ps["name"], 8 * n, [], []]
+            kernels = [kdot, kscal]
+
+            def step(timed):
+                if timed:
+                    ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev[0].record(s)
+                lift.lift_dot_v(vd, x, y, n, r)
+                if timed:
+                    ev2 = torch.cuda.Event(enable_timing=True)
+                    ev[1].record(s)
+                    kdot[2].append(ev[0]); kdot[3].append(ev[1])
+                    ev2.record(s)
+                lift.lift_scal_v(vs, n, float(alpha), x, z)
+                if timed:
+                    ev3 = torch.cuda.Event(enable_timing=True)
+                    ev3.record(s)
+                    kscal[2].append(ev2); kscal[3].append(ev3)
 
         def e2e_step(xp, yp, zp, rp):
             x.copy_(xp, non_blocking=True)
             y.copy_(yp, non_blocking=True)
-            lift.lift_dot_v(vd, x, y, n, r)
-            lift.lift_scal_v(vs, n, float(alpha), x, z)
+            if args.mode == "batched":
+                lift.lift_batch_run(hb2)
+            else:
+                calls()
             rp.copy_(r, non_blocking=True)
             zp.copy_(z, non_blocking=True)
 
@@ -213,6 +275,9 @@ def run_ours(args, rank, world, dist):
                     rp=torch.empty(1, dtype=torch.float32).pin_memory())
         h2d, d2h = 8 * n, 4 * n + 4
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pd["name"], ps["name"]],
+                  "submitted_as": ("one batched launch of the two calls (lift_batch_run)"
+                                   if args.mode == "batched" else
+                                   "two calls (lift_dot_v, lift_scal_v)"),
                   "l2": "no flush: inputs 3 x 256 MiB exceed the 129 MB L2"}
     elif wl == "mixed":
         n = WORKLOADS[wl]["n"]
@@ -463,21 +528,25 @@ def run_ours(args, rank, world, dist):
         ems = max_over_ranks(ems, dist, dev)
         e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
-    if wl == "dot_scal":
-        # context: the same step submitted as one 2-op batched launch
-        hb2 = lift.lift_batch_create([
-            {"op": lift.OP_DOT, "variant": -1, "n": n, "x": x, "y": y, "out": r},
-            {"op": lift.OP_SCAL, "variant": -1, "n": n, "alpha": float(alpha), "x": x, "out": z}])
+    if wl == "dot_scal" and args.no_extras:
+        lift.lift_batch_destroy(hb2)
+    elif wl == "dot_scal":
+        config["policy"] = policy
+        config["learned_vs_autotuned"] = learned_gap(
+            [(lift.OP_DOT, n, 0, 0), (lift.OP_SCAL, n, 0, 0)], {lift.OP_DOT: vd, lift.OP_SCAL: vs})
+        # context: the same step submitted the other way
+        other = calls if args.mode == "batched" else (lambda: lift.lift_batch_run(hb2))
         for _ in range(3):
-            lift.lift_batch_run(hb2)
+            other()
         a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a2.record(s)
         for _ in range(50):
-            lift.lift_batch_run(hb2)
+            other()
         b2.record(s)
         torch.cuda.synchronize()
-        config["same_step_as_one_batched_launch_gbs"] = round(
-            bytes_step * 50 / (a2.elapsed_time(b2) / 1e3) / 1e9, 1)
+        key = "same_step_as_two_calls_gbs" if args.mode == "batched" else \
+            "same_step_as_one_batched_launch_gbs"
+        config[key] = round(bytes_step * 50 / (a2.elapsed_time(b2) / 1e3) / 1e9, 1)
         lift.lift_batch_destroy(hb2)
     if wl == "batch":
         config["policies_gbs"] = policy_rates()
@@ -591,6 +660,14 @@ def main():
     ap.add_argument("--workload", default="dot_scal", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mlp", default=None, help="cost-model weights for the batch workload")
+    ap.add_argument("--variant", action="append",
+                    help="force a variant by name (repeatable), e.g. for a profiling capture")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the on-the-spot variant sweep and the other submission mode")
+    ap.add_argument("--mode", default="batched", choices=["batched", "calls"],
+                    help="dot_scal: submit the step as one batched launch or as two calls")
+    ap.add_argument("--fixed-policy", action="store_true",
+                    help="use the FIXED variant policy instead of the trained cost model")
     ap.add_argument("--batch-ops", type=int, default=20000,
                     help="ops of the batch workload (fewer only for profiling captures)")
     args = ap.parse_args()

@@ -177,8 +177,8 @@ static std::mutex g_policy_mu;
 // geometric-mean slowdown over the exhaustive GB300 sweep of 1,200 shapes
 // (variant names; looked up at first use).
 static const char* kDefaultName[LIFT_NUM_OPS] = {
-    "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t1024_v4_ldg", "gemv_w8_v4_u8",
-    "asum_bf16_t256_u4",    "dot_bf16_t256_u4",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4"};
+    "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t1024_v4_ldg", "gemv_tma_w8_c1024_s3",
+    "asum_bf16_t256_u4",    "dot_bf16_t256_u8",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4"};
 
 static int find_variant(int op, const char* name) {
   auto& L = registry(op);
