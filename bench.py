@@ -58,13 +58,19 @@ def peaks():
 
 
 KERNEL_SOURCE = {"asum": "reduce_f32.cu", "dot": "reduce_f32.cu", "scal": "scal_gemv.cu",
-                 "gemv": "scal_gemv.cu", "batch": "batch.cu", "mixed": "mixed.cu"}
+                 "gemv": "scal_gemv.cu", "batch": "batch.cu", "mixed": "mixed.cu",
+                 "gemv_tma": "gemv_tma.cu"}
 
 
 def kernel_hash(tag: str) -> str:
     """Hash of the source of the kernel a tag names (its .cu file and the
     shared device header): ncu counters taken on other sources are stale."""
-    op = "mixed" if ("bf16" in tag or "fp8" in tag) else tag.split("_", 1)[0]
+    if "bf16" in tag or "fp8" in tag:
+        op = "mixed"
+    elif tag.startswith("gemv_tma"):
+        op = "gemv_tma"
+    else:
+        op = tag.split("_", 1)[0]
     d = os.path.join(ROOT, "paper_1502_02389_gb300", "csrc")
     h = hashlib.sha256()
     for f in (KERNEL_SOURCE.get(op, ""), "lift_internal.cuh"):

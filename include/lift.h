@@ -69,8 +69,15 @@ typedef enum {
   LIFT_OP_DOT_BF16 = 5,
   LIFT_OP_ASUM_FP8 = 6,
   LIFT_OP_DOT_FP8 = 7,
-  LIFT_NUM_OPS = 8
+  LIFT_OP_NRM2 = 8,
+  LIFT_OP_SUM = 9,
+  LIFT_OP_AXPY = 10,
+  LIFT_NUM_OPS = 11
 } lift_op;
+
+/* The cost model covers op ids 0 .. LIFT_MLP_OPS-1; the MLP policy falls
+ * back to the FIXED choice for the others. */
+#define LIFT_MLP_OPS 8
 
 /* ------------------------------------------------------------------------
  * Library state
@@ -121,6 +128,28 @@ lift_status lift_scal(int64_t n, float alpha, const float* x, float* y, void* st
  * Per row: z = fl(alpha * dot); y = fl(z + fl(beta * y)). */
 lift_status lift_gemv(int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
                       const float* x, float beta, float* y, void* stream);
+
+/* ------------------------------------------------------------------------
+ * More programs through the same kernel templates: the code generator of
+ * the paper only knows reduce-seq and the maps (Sec. 4.2, "Reduction"), so
+ * any user function plugs into the same kernels.
+ *   nrm2(x)       = map(sqrt) . reduce(add, 0) . map(square, x):
+ *                   sqrt(sum x_i^2), the sum combined in FP64 and its
+ *                   correctly rounded FP64 square root rounded once to fp32
+ *   sum(x)        = reduce(add, 0)(x)
+ *   axpy(a, x, y) = map(add) . zip(map(mult(a), x), y): y_i <- fl(fl(a x_i) + y_i),
+ *                   in place in y (y == x allowed; other overlaps are not)
+ * Arguments, errors and conventions as for asum / scal.
+ * ------------------------------------------------------------------------ */
+lift_status lift_nrm2(const float* x, int64_t n, float* result, void* stream);
+lift_status lift_sum(const float* x, int64_t n, float* result, void* stream);
+lift_status lift_axpy(int64_t n, float alpha, const float* x, float* y, void* stream);
+lift_status lift_nrm2_v(int variant, const float* x, int64_t n, float* result, double* result_f64,
+                        void* stream);
+lift_status lift_sum_v(int variant, const float* x, int64_t n, float* result, double* result_f64,
+                       void* stream);
+lift_status lift_axpy_v(int variant, int64_t n, float alpha, const float* x, float* y,
+                        void* stream);
 
 /* ------------------------------------------------------------------------
  * Explicit variants (the autotuner's interface).  `variant` indexes the
@@ -206,7 +235,8 @@ lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
 /* The 10 cost-model features of a call, written to out[0..9]: one-hot op
  * family (asum, dot, scal, gemv), log2(n+1)/32, log2(M+1)/16,
  * log2(N+1)/16, one-hot element type (fp32, bf16, fp8).  For gemv the
- * size feature uses n = M*N.  Host-only; needs no device. */
+ * size feature uses n = M*N.  Host-only; needs no device.  Defined for op
+ * ids below LIFT_MLP_OPS (LIFT_ERR_INVALID_ARG otherwise). */
 lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out);
 
 /* ------------------------------------------------------------------------

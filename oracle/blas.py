@@ -28,7 +28,7 @@ import math
 import numpy as np
 
 from .patterns import (C, Join, Map, Reduce, Zip, ZipWith, abs_, add, evaluate,
-                       mult, mult_by)
+                       mult, mult_by, sqrt64, square)
 
 U_FP32 = 2.0 ** -24
 
@@ -55,6 +55,54 @@ def gemv_z_expr(a):
 def gemv_y_expr():
     """y' = map(add) . zip(z, scal(b, y))."""
     return C(Map(add), Zip())
+
+
+# ---------------------------------------------------------------------------
+# user-function programs in the same style (the code generator only knows
+# reduce-seq and the maps; any user functions plug in, Sec. 4.2 "Reduction")
+#   nrm2(x)       = map(sqrt) . reduce(add, 0) . map(square, x)
+#   sum(x)        = reduce(add, 0)(x)
+#   axpy(a, x, y) = map(add) . zip(map(mult(a), x), y)
+# ---------------------------------------------------------------------------
+def nrm2_expr():
+    return C(Map(sqrt64), Reduce(add, 0), Map(square))
+
+
+def sum_expr():
+    return Reduce(add, 0)
+
+
+def axpy_expr():
+    """Applied to the pair (scal(a, x), y)."""
+    return C(Map(add), Zip())
+
+
+def nrm2(x, mode="f64") -> float:
+    x = np.asarray(x)
+    if x.size == 0:
+        return 0.0
+    return float(evaluate(nrm2_expr(), x, mode)[0])
+
+
+def sum_(x, mode="f64") -> float:
+    x = np.asarray(x)
+    if x.size == 0:
+        return 0.0
+    return float(evaluate(sum_expr(), x, mode)[0])
+
+
+def axpy(a, x, y, mode="f64"):
+    x, y = np.asarray(x), np.asarray(y)
+    return evaluate(axpy_expr(), (scal(a, x, mode), y), mode)
+
+
+def nrm2_tolerance(n: int, sum_sq: float) -> float:
+    """nrm2 = sqrt(S) with S = sum x_i^2 (all terms >= 0, so sum|terms| = S).
+    An error e <= 4 u ceil(log2 n) S in S moves the root by
+    e / (sqrt(S') + sqrt(S)) <= e / sqrt(S) = 4 u ceil(log2 n) sqrt(S); the
+    final rounding to fp32 adds at most u sqrt(S') (bounded by 2 u sqrt(S)):
+    (4 ceil(log2 n) + 2) u sqrt(S)."""
+    return (4 * depth(n) + 2) * U_FP32 * math.sqrt(float(sum_sq))
 
 
 def scal(a, x, mode="f64"):

@@ -20,7 +20,11 @@ from .patterns import (AsScalar, AsVector, C, Id, Iterate, Join, Map, MapLocal,
                        MapSeq, MapWorkgroup, PadTo, PartRed, Reduce, ReduceSeq,
                        Reorder, ReorderStride, Split, ToGlobal, ToLocal, Vect, Zip,
                        ZipWith, abs_, absAndPlus, add, add64, fold, id_, mul3,
-                       mult, mult_by, to_f32, to_f64)
+                       mult, mult_by, sqrt64, square, to_f32, to_f64)
+
+# the fused reduction function of each reduce program (rule 3f applied to
+# reduce(add, 0) . map(g)); sum has no map and folds add itself
+FOLD = {"asum": absAndPlus, "dot": fold(add, mult), "nrm2": fold(add, square), "sum": add}
 
 
 # ============================================================================
@@ -123,14 +127,17 @@ def _thread_order(threads: int, per_thread: int, J: int, stride: bool):
     return C(Split(per_thread), Join(), ReorderStride(s=threads), Split(J))
 
 
-def final_combine(P: int, ft: int, cast32: bool = True):
+def final_combine(P: int, ft: int, cast32: bool = True, post=None):
     """[P] fp32 partials -> [1]: thread t of one CTA of ft threads sums
-    partials t, t+ft, ... in FP64, then an FP64 block tree; the result is
+    partials t, t+ft, ... in FP64, then an FP64 block tree; ``post`` (a user
+    function such as sqrt64) is mapped over the FP64 sum; the result is
     rounded to fp32 when cast32."""
     M = max(1, math.ceil(P / ft))
     body = C(block_tree(ft, add64), Join(),
              MapLocal(ReduceSeq(add64, 0)), Split(M), ReorderStride(s=ft),
              PadTo(ft * M), Map(to_f64))
+    if post is not None:
+        body = C(Map(post), body)
     if cast32:
         body = C(Map(to_f32), body)
     return C(Join(), MapWorkgroup(body), Split(P))
@@ -142,7 +149,7 @@ def cta_expr(op: str, K: int, tile: int, vw: int, threads: int, stride: bool = T
     V = tile // vw
     J = V // threads
     assert V % threads == 0 and tile % vw == 0
-    f = absAndPlus if op == "asum" else fold(add, mult)
+    f = FOLD[op]
     fr = Vect(vw, f) if vw > 1 else f
     lanes = Id()
     if vw > 1:
@@ -180,7 +187,7 @@ def reduce_variant(op: str, n: int, tile: int, vw: int, threads: int, grid: int,
     fold), adds its lanes in order, then the CTA runs ``block_tree``; with a
     cluster, ``cluster`` consecutive CTA results are added in rank order;
     the partials are combined by ``final_combine``."""
-    if op not in ("asum", "dot"):
+    if op not in FOLD:
         raise ValueError(op)
     T = max(1, math.ceil(n / tile))
     K = math.ceil(T / grid)
@@ -195,7 +202,7 @@ def reduce_variant(op: str, n: int, tile: int, vw: int, threads: int, grid: int,
     if cluster > 1:
         parts = C(Join(), Map(ReduceSeq(add, 0)), Split(cluster), parts)
         P = grid // cluster
-    e = C(final_combine(P, ft, cast32), parts)
+    e = C(final_combine(P, ft, cast32, sqrt64 if op == "nrm2" else None), parts)
     if op == "dot":
         e = C(e, Zip())
     return e, L

@@ -91,7 +91,8 @@ class UserFun:
 
 
 ARITY = {"abs": 1, "id": 1, "mul3": 1, "mult_by": 1, "to_f32": 1, "to_f64": 1,
-         "neg": 1, "add": 2, "add64": 2, "mult": 2, "fold": 2, "compose": 1}
+         "neg": 1, "add": 2, "add64": 2, "mult": 2, "fold": 2, "compose": 1,
+         "square": 1, "sqrt64": 1}
 
 abs_ = UserFun("abs")          # Fig. 5: abs(x) = if (x < 0) -x else x
 id_ = UserFun("id")
@@ -102,6 +103,8 @@ neg = UserFun("neg")
 add64 = UserFun("add64")       # x + y always in FP64 (combine steps)
 to_f32 = UserFun("to_f32")     # round to fp32 (the store of an fp32 result)
 to_f64 = UserFun("to_f64")     # widen to fp64 (exact)
+square = UserFun("square")     # x * x
+sqrt64 = UserFun("sqrt64")     # correctly rounded square root, always in FP64
 
 
 def mult_by(a) -> UserFun:
@@ -582,6 +585,10 @@ class _Arith:
             return r
         if n == "mult":
             return args[0] * args[1]
+        if n == "square":
+            return args[0] * args[0]
+        if n == "sqrt64":
+            return np.sqrt(np.asarray(args[0], np.float64))
         if n == "mul3":
             return args[0] * self.const(3)
         if n == "mult_by":

@@ -36,7 +36,7 @@ def offsets(records: Optional[List[Dict]] = None) -> Tuple[List[int], int]:
     (a variant added to the library later stays out of the model's picks
     until the model is retrained); otherwise the library's current lists."""
     off, v = [], 0
-    for op in range(lift.NUM_OPS):
+    for op in range(lift.MLP_OPS):
         off.append(v)
         if records is None:
             v += lift.lift_variant_count(op)
@@ -185,7 +185,7 @@ def best_fixed(records: List[Dict]) -> Dict[int, int]:
     the given shapes (the paper's one fixed derivation per device)."""
     g = group(records)
     best = {}
-    for op in range(lift.NUM_OPS):
+    for op in range(lift.MLP_OPS):
         rows = [t for (o, *_), t in g.items() if o == op]
         if not rows:
             continue

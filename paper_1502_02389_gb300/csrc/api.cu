@@ -91,16 +91,21 @@ static lift_status init_device(int device) {
 // registry
 // ---------------------------------------------------------------------------
 void register_gemv_tma(std::vector<Variant>& gemv);   // gemv_tma.cu
+void register_reduce_f32(std::vector<Variant>& asum, std::vector<Variant>& dot,
+                         std::vector<Variant>& nrm2, std::vector<Variant>& sum);  // reduce_f32.cu
+void register_axpy(std::vector<Variant>& axpy);       // scal_gemv.cu
 
 static std::vector<Variant> g_ops[LIFT_NUM_OPS];
 static std::once_flag g_reg_once;
 
 static void build_registry() {
-  register_reduce_f32(g_ops[LIFT_OP_ASUM], g_ops[LIFT_OP_DOT]);
+  register_reduce_f32(g_ops[LIFT_OP_ASUM], g_ops[LIFT_OP_DOT], g_ops[LIFT_OP_NRM2],
+                      g_ops[LIFT_OP_SUM]);
   register_scal(g_ops[LIFT_OP_SCAL]);
   register_gemv(g_ops[LIFT_OP_GEMV]);
   register_gemv_tma(g_ops[LIFT_OP_GEMV]);
   register_mixed(g_ops);
+  register_axpy(g_ops[LIFT_OP_AXPY]);
 }
 
 std::vector<Variant>& registry(int op) {
@@ -163,12 +168,12 @@ struct TableEntry {
 
 struct Mlp {
   int d_in = 0, h1 = 0, h2 = 0, V = 0;
-  int offsets[LIFT_NUM_OPS] = {0};
+  int offsets[LIFT_MLP_OPS] = {0};
   std::vector<float> W1, b1, W2, b2, W3, b3;
 };
 
 static int g_policy = LIFT_POLICY_FIXED;
-static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1};
+static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 static std::vector<TableEntry> g_table[LIFT_NUM_OPS];
 static Mlp g_mlp;
 static std::mutex g_policy_mu;
@@ -178,7 +183,8 @@ static std::mutex g_policy_mu;
 // (variant names; looked up at first use).
 static const char* kDefaultName[LIFT_NUM_OPS] = {
     "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t1024_v4_ldg", "gemv_tma_w8_c1024_s3",
-    "asum_bf16_t256_u4",    "dot_bf16_t256_u8",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4"};
+    "asum_bf16_t256_u4",    "dot_bf16_t256_u8",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4",
+    "nrm2_t4096_v4_ldg_p1", "sum_t4096_v4_ldg_p1", "axpy_t1024_v4_ldg"};
 
 static int find_variant(int op, const char* name) {
   auto& L = registry(op);
@@ -198,9 +204,9 @@ extern "C" {
 // scal, gemv), log2(n+1)/32, log2(M+1)/16, log2(N+1)/16, one-hot dtype
 // (fp32, bf16, fp8).  For gemv n = M*N.
 lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out) {
-  if (op < 0 || op >= LIFT_NUM_OPS || !out) return LIFT_ERR_INVALID_ARG;
-  static const int fam[LIFT_NUM_OPS] = {0, 1, 2, 3, 0, 1, 0, 1};
-  static const int dt[LIFT_NUM_OPS] = {0, 0, 0, 0, 1, 1, 2, 2};
+  if (op < 0 || op >= LIFT_MLP_OPS || !out) return LIFT_ERR_INVALID_ARG;
+  static const int fam[LIFT_MLP_OPS] = {0, 1, 2, 3, 0, 1, 0, 1};
+  static const int dt[LIFT_MLP_OPS] = {0, 0, 0, 0, 1, 1, 2, 2};
   for (int i = 0; i < 10; ++i) out[i] = 0.f;
   out[fam[op]] = 1.f;
   if (op == LIFT_OP_GEMV) n = M * N;
@@ -232,7 +238,7 @@ static int mlp_pick(int op, int64_t n, int64_t M, int64_t N) {
   }
   // variants the weights know: the file's slice of this op (a registry that
   // grew after training keeps its newer variants out of the pick)
-  const int file_cnt = (op + 1 < LIFT_NUM_OPS ? m.offsets[op + 1] : m.V) - m.offsets[op];
+  const int file_cnt = (op + 1 < LIFT_MLP_OPS ? m.offsets[op + 1] : m.V) - m.offsets[op];
   const int cnt = std::min((int)registry(op).size(), file_cnt);
   int best = 0;
   float best_t = INFINITY;
@@ -270,7 +276,7 @@ static int pick_variant(int op, int64_t n, int64_t M, int64_t N) {
   std::lock_guard<std::mutex> lk(g_policy_mu);
   if (g_override[op] >= 0) return g_override[op];
   int v = -1;
-  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0) v = mlp_pick(op, n, M, N);
+  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < LIFT_MLP_OPS) v = mlp_pick(op, n, M, N);
   if (g_policy == LIFT_POLICY_TABLE) v = table_pick(op, n, M, N);
   if (v < 0) v = find_variant(op, kDefaultName[op]);
   return v;
@@ -494,6 +500,58 @@ lift_status lift_dot_ex(lift_dtype t, const void* x, const float* xscale, const 
   return lift_dot_ex_v(-1, t, x, xscale, y, yscale, n, result, result_f64, stream);
 }
 
+lift_status lift_nrm2_v(int variant, const float* x, int64_t n, float* result, double* result_f64,
+                        void* stream) {
+  if (bad_n(n) || !result || (n > 0 && !x) || !aligned(x, 4))
+    return set_error(LIFT_ERR_INVALID_ARG, "nrm2 arguments");
+  Args a;
+  a.x = x;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(LIFT_OP_NRM2, variant, a, stream);
+}
+
+lift_status lift_sum_v(int variant, const float* x, int64_t n, float* result, double* result_f64,
+                       void* stream) {
+  if (bad_n(n) || !result || (n > 0 && !x) || !aligned(x, 4))
+    return set_error(LIFT_ERR_INVALID_ARG, "sum arguments");
+  Args a;
+  a.x = x;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(LIFT_OP_SUM, variant, a, stream);
+}
+
+lift_status lift_axpy_v(int variant, int64_t n, float alpha, const float* x, float* y, void* stream) {
+  if (bad_n(n) || (n > 0 && (!x || !y))) return set_error(LIFT_ERR_INVALID_ARG, "axpy arguments");
+  if (!aligned(x, 4) || !aligned(y, 4)) return set_error(LIFT_ERR_INVALID_ARG, "x/y not 4-byte aligned");
+  if (n > 0 && x != y) {
+    const char* xb = (const char*)x;
+    const char* yb = (const char*)y;
+    if (xb < yb + n * 4 && yb < xb + n * 4)
+      return set_error(LIFT_ERR_INVALID_ARG, "x and y overlap without being equal");
+  }
+  if (n == 0) return LIFT_OK;
+  Args a;
+  a.x = x;
+  a.out = y;
+  a.n = n;
+  a.alpha = alpha;
+  return run(LIFT_OP_AXPY, variant, a, stream);
+}
+
+lift_status lift_nrm2(const float* x, int64_t n, float* result, void* stream) {
+  return lift_nrm2_v(-1, x, n, result, nullptr, stream);
+}
+lift_status lift_sum(const float* x, int64_t n, float* result, void* stream) {
+  return lift_sum_v(-1, x, n, result, nullptr, stream);
+}
+lift_status lift_axpy(int64_t n, float alpha, const float* x, float* y, void* stream) {
+  return lift_axpy_v(-1, n, alpha, x, y, stream);
+}
+
 int lift_variant_count(int op) {
   if (op < 0 || op >= LIFT_NUM_OPS) return 0;
   return (int)registry(op).size();
@@ -568,7 +626,7 @@ lift_status lift_set_policy(int policy, const char* path) {
     if (!(f >> tag >> ver >> m.d_in >> m.h1 >> m.h2 >> m.V) || tag != "lift-mlp" || m.d_in != 10)
       return set_error(LIFT_ERR_INVALID_ARG, "bad MLP header");
     if (!(f >> off) || off != "offsets") return set_error(LIFT_ERR_INVALID_ARG, "bad MLP offsets");
-    for (int i = 0; i < LIFT_NUM_OPS; ++i) f >> m.offsets[i];
+    for (int i = 0; i < LIFT_MLP_OPS; ++i) f >> m.offsets[i];
     auto rd = [&](std::vector<float>& w, size_t cnt) {
       w.resize(cnt);
       for (size_t i = 0; i < cnt; ++i)

@@ -34,13 +34,27 @@ namespace cg = cooperative_groups;
 namespace lift {
 namespace {
 
+// The fused reduction function lambda acc, x: acc + g(x) of each program
+// (rule 3f applied to reduce(add, 0) . map(g)): g = abs (asum), mult over
+// the zipped pair (dot), square (nrm2), none (sum).
 template <int OP>
 __device__ __forceinline__ float fold_term(float acc, float a, float b) {
   if constexpr (OP == LIFT_OP_ASUM) {
     return __fadd_rn(acc, fabsf(a));
-  } else {
+  } else if constexpr (OP == LIFT_OP_DOT) {
     return __fadd_rn(acc, __fmul_rn(a, b));
+  } else if constexpr (OP == LIFT_OP_NRM2) {
+    return __fadd_rn(acc, __fmul_rn(a, a));
+  } else {
+    return __fadd_rn(acc, a);
   }
+}
+
+// map(post) over the FP64 reduce result: sqrt for nrm2 (correctly rounded)
+template <int OP>
+__device__ __forceinline__ double post(double s) {
+  if constexpr (OP == LIFT_OP_NRM2) return __dsqrt_rn(s);
+  return s;
 }
 
 template <int OP, int VW>
@@ -56,7 +70,7 @@ __device__ __forceinline__ int vec_index(int t, int j) {
 }
 
 // CTA result -> (cluster) -> partials -> (one pass) final FP64 combine.
-template <int THREADS, int CLUSTER, bool ONEPASS>
+template <int OP, int THREADS, int CLUSTER, bool ONEPASS>
 __device__ __forceinline__ void finish(float r, float* red, double* red64, float* partials,
                                        unsigned* ticket, float* result, double* result64) {
   r = block_tree<THREADS>(r, red);
@@ -89,7 +103,7 @@ __device__ __forceinline__ void finish(float r, float* red, double* red64, float
     __syncthreads();
     if (is_last) {
       __threadfence();
-      const double s = combine_partials<THREADS>(partials, P, red64);
+      const double s = post<OP>(combine_partials<THREADS>(partials, P, red64));
       if (threadIdx.x == 0) {
         *result = static_cast<float>(s);
         if (result64) *result64 = s;
@@ -164,7 +178,7 @@ __global__ void __launch_bounds__(THREADS)
   float r = acc[0];
 #pragma unroll
   for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
-  finish<THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
+  finish<OP, THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
   (void)status;
 }
 
@@ -240,14 +254,14 @@ __global__ void __launch_bounds__(THREADS)
   float r = acc[0];
 #pragma unroll
   for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
-  finish<THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
+  finish<OP, THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
 }
 
-template <int FT>
+template <int OP, int FT>
 __global__ void __launch_bounds__(FT)
     combine_kernel(const float* __restrict__ partials, int64_t P, float* result, double* result64) {
   __shared__ double red64[kWarp];
-  const double s = combine_partials<FT>(partials, P, red64);
+  const double s = post<OP>(combine_partials<FT>(partials, P, red64));
   if (threadIdx.x == 0) {
     *result = static_cast<float>(s);
     if (result64) *result64 = s;
@@ -299,7 +313,8 @@ struct ReduceF32 {
     lift_status rc = launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), CLUSTER, s, args);
     if (rc != LIFT_OK || PASSES == 1) return rc;
     const int64_t P = g / CLUSTER;
-    combine_kernel<kCombineThreads><<<1, kCombineThreads, 0, s>>>(partials, P, a.result, a.result64);
+    combine_kernel<OP, kCombineThreads><<<1, kCombineThreads, 0, s>>>(partials, P, a.result,
+                                                                       a.result64);
     return cuda_check(cudaGetLastError(), "combine launch");
   }
 };
@@ -318,7 +333,8 @@ Variant make_variant(const char* name) {
   v.info.passes = PASSES;
   v.info.stages = STAGES;
   v.info.final_threads = PASSES == 1 ? THREADS : kCombineThreads;
-  snprintf(v.info.name, sizeof(v.info.name), "%s_%s", OP == LIFT_OP_ASUM ? "asum" : "dot", name);
+  const char* prefix = OP == LIFT_OP_ASUM ? "asum" : OP == LIFT_OP_DOT ? "dot" : OP == LIFT_OP_NRM2 ? "nrm2" : "sum";
+  snprintf(v.info.name, sizeof(v.info.name), "%s_%s", prefix, name);
   v.launch = &K::launch;
   v.grid = &K::grid;
   v.align_bytes = STAGES > 0 ? 16 : VW * (int)sizeof(float);
@@ -373,12 +389,26 @@ Variant make_variant(const char* name) {
   L.push_back(make_variant<OP, 256, 4096, 1, false, 0, 1, 1>("chunk_t4096_v1_ldg_p1")); \
   L.push_back(make_variant<OP, 256, 4096, 4, false, 4, 1, 1>("chunk_t4096_v4_tma4_p1"));
 
+// nrm2 and sum: the same templates with other user functions; a compact
+// set of the variants that lead the asum / dot sweeps.
+#define LIFT_REDUCE_VARIANTS_SHORT(OP, L)                                   \
+  L.push_back(make_variant<OP, 256, 1024, 1, true, 0, 1, 1>("t1024_v1_ldg_p1"));  \
+  L.push_back(make_variant<OP, 256, 4096, 4, true, 0, 1, 1>("t4096_v4_ldg_p1"));  \
+  L.push_back(make_variant<OP, 256, 4096, 4, true, 0, 1, 2>("t4096_v4_ldg_p2"));  \
+  L.push_back(make_variant<OP, 256, 2048, 8, true, 0, 1, 1>("t2048_v8_ldg_p1"));  \
+  L.push_back(make_variant<OP, 256, 4096, 4, true, 4, 1, 1>("t4096_v4_tma4_p1")); \
+  L.push_back(make_variant<OP, 256, 4096, 4, true, 0, 2, 1>("c2_t4096_v4_ldg_p1")); \
+  L.push_back(make_variant<OP, 32, 1024, 8, true, 0, 1, 1>("w32_t1024_v8_ldg_p1"));
+
 }  // namespace
 
-void register_reduce_f32(std::vector<Variant>& asum, std::vector<Variant>& dot) {
+void register_reduce_f32(std::vector<Variant>& asum, std::vector<Variant>& dot,
+                         std::vector<Variant>& nrm2, std::vector<Variant>& sum) {
   LIFT_REDUCE_VARIANTS(LIFT_OP_ASUM, asum)
   LIFT_REDUCE_VARIANTS(LIFT_OP_DOT, dot)
-  for (auto* L : {&asum, &dot})
+  LIFT_REDUCE_VARIANTS_SHORT(LIFT_OP_NRM2, nrm2)
+  LIFT_REDUCE_VARIANTS_SHORT(LIFT_OP_SUM, sum)
+  for (auto* L : {&asum, &dot, &nrm2, &sum})
     for (size_t i = 0; i < L->size(); ++i) {
       (*L)[i].info.id = static_cast<int>(i);
       (*L)[i].fallback = 0;  // t1024_v1_ldg_p1: 4-byte loads only

@@ -178,6 +178,84 @@ Variant scal_variant(const char* name) {
 }
 
 // ---------------------------------------------------------------------------
+// axpy = map(add) . zip(map(mult(alpha), x), y): the scal map with a second
+// zipped input; y_i <- fl(fl(alpha * x_i) + y_i), one rounding per operation
+// ---------------------------------------------------------------------------
+template <int THREADS, int TILE, int VW>
+__global__ void __launch_bounds__(THREADS)
+    axpy_ldg(int64_t n, float alpha, const float* x, float* y) {
+  constexpr int J = TILE / VW / THREADS;
+  static_assert(J >= 1 && (TILE / VW) % THREADS == 0, "tile too small");
+  const int64_t full = n / TILE;
+  int64_t tile = blockIdx.x;
+  for (; tile < full; tile += gridDim.x) {
+    Vec<VW> a[J], b[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int64_t e = tile * TILE + (int64_t)(threadIdx.x + THREADS * j) * VW;
+      ld_stream(x + e, a[j]);
+      ld_stream(y + e, b[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+#pragma unroll
+      for (int l = 0; l < VW; ++l) b[j].v[l] = __fadd_rn(__fmul_rn(alpha, a[j].v[l]), b[j].v[l]);
+      st_stream(y + tile * TILE + (int64_t)(threadIdx.x + THREADS * j) * VW, b[j]);
+    }
+  }
+  if (tile == full && full * TILE < n) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int64_t first = tile * TILE + (int64_t)(threadIdx.x + THREADS * j) * VW;
+#pragma unroll
+      for (int l = 0; l < VW; ++l)
+        if (first + l < n) y[first + l] = __fadd_rn(__fmul_rn(alpha, x[first + l]), y[first + l]);
+    }
+  }
+}
+
+template <int THREADS, int TILE, int VW>
+struct Axpy {
+  static const void* kernel() { return reinterpret_cast<const void*>(&axpy_ldg<THREADS, TILE, VW>); }
+  static int64_t grid(const Variant&, const Args& a) {
+    const int64_t T = a.n > 0 ? (a.n + TILE - 1) / TILE : 1;
+    const int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
+    if (g <= 0) return 0;
+    const int64_t per = (T + g - 1) / g;
+    return (T + per - 1) / per;
+  }
+  static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
+    const int64_t g = grid(v, a);
+    if (g <= 0) return set_error(LIFT_ERR_CUDA, std::string("no resident CTA for ") + v.info.name);
+    int64_t n = a.n;
+    float alpha = a.alpha;
+    const float* x = static_cast<const float*>(a.x);
+    float* y = a.out;
+    void* args[] = {&n, &alpha, &x, &y};
+    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args);
+  }
+};
+
+template <int THREADS, int TILE, int VW>
+Variant axpy_variant(const char* name) {
+  using K = Axpy<THREADS, TILE, VW>;
+  Variant v{};
+  v.info.op = LIFT_OP_AXPY;
+  v.info.tile = TILE;
+  v.info.vw = VW;
+  v.info.threads = THREADS;
+  v.info.stride = 1;
+  v.info.cluster = 1;
+  v.info.passes = 1;
+  snprintf(v.info.name, sizeof(v.info.name), "axpy_%s", name);
+  v.launch = &K::launch;
+  v.grid = &K::grid;
+  v.align_bytes = VW * 4;
+  v.fallback = 0;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
 // gemv
 // ---------------------------------------------------------------------------
 template <int VW>
@@ -328,6 +406,15 @@ void register_scal(std::vector<Variant>& L) {
   L.push_back(scal_variant<256, 4096, 4, 4>("t4096_tma4"));
   L.push_back(scal_variant<256, 4096, 4, 2>("t4096_tma2"));
   L.push_back(scal_variant<256, 4096, 4, 6>("t4096_tma6"));
+  for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
+}
+
+void register_axpy(std::vector<Variant>& L) {
+  L.push_back(axpy_variant<256, 1024, 1>("t1024_v1_ldg"));
+  L.push_back(axpy_variant<256, 1024, 4>("t1024_v4_ldg"));
+  L.push_back(axpy_variant<256, 2048, 4>("t2048_v4_ldg"));
+  L.push_back(axpy_variant<256, 4096, 4>("t4096_v4_ldg"));
+  L.push_back(axpy_variant<256, 2048, 8>("t2048_v8_ldg"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 

@@ -19,9 +19,12 @@ LIB_PATH = os.path.join(HERE, "liftblas.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NO_MEMORY, ERR_TIMEOUT, ERR_NOT_INITIALIZED = range(7)
 F32, BF16, FP8_E4M3 = 0, 1, 2
-OP_ASUM, OP_DOT, OP_SCAL, OP_GEMV, OP_ASUM_BF16, OP_DOT_BF16, OP_ASUM_FP8, OP_DOT_FP8 = range(8)
-NUM_OPS = 8
-OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8"]
+(OP_ASUM, OP_DOT, OP_SCAL, OP_GEMV, OP_ASUM_BF16, OP_DOT_BF16, OP_ASUM_FP8, OP_DOT_FP8, OP_NRM2,
+ OP_SUM, OP_AXPY) = range(11)
+NUM_OPS = 11
+MLP_OPS = 8     # op ids the cost model covers
+OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8", "nrm2",
+            "sum", "axpy"]
 POLICY_FIXED, POLICY_TABLE, POLICY_MLP = 0, 1, 2
 
 
@@ -75,6 +78,12 @@ _SIGS = {
     "lift_pick": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lift_features": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "lift_asum_noalloc": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_nrm2": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_sum": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_axpy": ([_I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
+    "lift_nrm2_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_sum_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_axpy_v": ([ctypes.c_int, _I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
     "lift_batch_create": ([ctypes.c_void_p, _I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "lift_batch_run": ([_P, _P], ctypes.c_int),
     "lift_batch_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
@@ -197,6 +206,32 @@ def lift_scal_v(variant, n, alpha, x, y, stream=None):
 def lift_gemv_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
     _check(lib().lift_gemv_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
                              _stream(stream)), "lift_gemv_v")
+
+
+def lift_nrm2(x, n, result, stream=None):
+    _check(lib().lift_nrm2(_ptr(x), n, _ptr(result), _stream(stream)), "lift_nrm2")
+
+
+def lift_sum(x, n, result, stream=None):
+    _check(lib().lift_sum(_ptr(x), n, _ptr(result), _stream(stream)), "lift_sum")
+
+
+def lift_axpy(n, alpha, x, y, stream=None):
+    _check(lib().lift_axpy(n, alpha, _ptr(x), _ptr(y), _stream(stream)), "lift_axpy")
+
+
+def lift_nrm2_v(variant, x, n, result, result_f64=None, stream=None):
+    _check(lib().lift_nrm2_v(variant, _ptr(x), n, _ptr(result), _ptr(result_f64), _stream(stream)),
+           "lift_nrm2_v")
+
+
+def lift_sum_v(variant, x, n, result, result_f64=None, stream=None):
+    _check(lib().lift_sum_v(variant, _ptr(x), n, _ptr(result), _ptr(result_f64), _stream(stream)),
+           "lift_sum_v")
+
+
+def lift_axpy_v(variant, n, alpha, x, y, stream=None):
+    _check(lib().lift_axpy_v(variant, n, alpha, _ptr(x), _ptr(y), _stream(stream)), "lift_axpy_v")
 
 
 def lift_asum_ex(dtype, x, xscale, n, result, result_f64=None, stream=None):

@@ -32,8 +32,10 @@ MIXED = (lift.OP_ASUM_BF16, lift.OP_DOT_BF16, lift.OP_ASUM_FP8, lift.OP_DOT_FP8)
 
 def op_bytes(op: int, n: int, M: int = 0, N: int = 0) -> int:
     """Algorithmic bytes one call moves."""
-    if op == lift.OP_ASUM:
+    if op in (lift.OP_ASUM, lift.OP_NRM2, lift.OP_SUM):
         return 4 * n
+    if op == lift.OP_AXPY:
+        return 12 * n
     if op == lift.OP_DOT:
         return 8 * n
     if op == lift.OP_SCAL:
@@ -114,9 +116,14 @@ class Buffers:
         """The r-th call of the rotation for variant vid."""
         op, n, M, N = self.op, self.n, self.M, self.N
         res = self.res[64 * r:64 * r + 1]
-        if op == lift.OP_ASUM:
+        if op in (lift.OP_ASUM, lift.OP_NRM2, lift.OP_SUM):
             x = self._slice("x", "f32", r, n)
-            return lambda: lift.lift_asum_v(vid, x, n, res)
+            fn = {lift.OP_ASUM: lift.lift_asum_v, lift.OP_NRM2: lift.lift_nrm2_v,
+                  lift.OP_SUM: lift.lift_sum_v}[op]
+            return lambda: fn(vid, x, n, res)
+        if op == lift.OP_AXPY:
+            x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
+            return lambda: lift.lift_axpy_v(vid, n, 1.5, x, y)
         if op == lift.OP_DOT:
             x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
             return lambda: lift.lift_dot_v(vid, x, y, n, res)
@@ -287,6 +294,7 @@ def workload_shapes() -> List[Tuple[int, int, int, int]]:
          (lift.OP_ASUM, 1 << 26, 0, 0),
          (lift.OP_GEMV, 8192 * 8192, 8192, 8192), (lift.OP_GEMV, 65536 * 1024, 65536, 1024)]
     s += [(op, 1 << 28, 0, 0) for op in MIXED]
+    s += [(op, 1 << 26, 0, 0) for op in (lift.OP_NRM2, lift.OP_SUM, lift.OP_AXPY)]
     return s
 
 
@@ -295,7 +303,7 @@ def random_shapes(count: int, seed: int, ops: Optional[List[int]] = None,
     """Shapes for the cost model: op uniform over ``ops``; vector lengths
     round(2^U(lo, hi)); gemv M, N = round(2^U(6, 14)) with M*N <= 2^28."""
     rng = np.random.default_rng(seed)
-    ops = ops or list(range(lift.NUM_OPS))
+    ops = ops or list(range(lift.MLP_OPS))
     out = []
     while len(out) < count:
         op = int(rng.choice(ops))

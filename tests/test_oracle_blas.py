@@ -119,3 +119,49 @@ def test_tolerance_formula():
     assert blas.tolerance(1, 3.0) == 4 * u * 1 * 3.0
     assert blas.tolerance(3, 1.0) == 4 * u * 2
     assert blas.tolerance(1000, 1.0) == 4 * u * 10
+
+
+# ---------------------------------------------------------------------------
+# user-function programs: nrm2, sum, axpy
+# ---------------------------------------------------------------------------
+def test_nrm2_closed_forms():
+    assert blas.nrm2(np.array([3.0, 4.0])) == 5.0
+    assert blas.nrm2(np.array([-3.0, 4.0])) == 5.0          # the square removes the sign
+    for k in range(0, 12, 3):
+        assert blas.nrm2(np.ones(4 ** k)) == 2.0 ** k        # sqrt(4^k)
+    assert blas.nrm2(np.zeros(0)) == 0.0
+
+
+def test_sum_closed_forms_and_signs():
+    for n in (1, 7, 1 << 14):
+        i = np.arange(n, dtype=float)
+        assert blas.sum_(i) == n * (n - 1) / 2
+        assert blas.sum_(-i) == -n * (n - 1) / 2              # no abs: signs stay
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nrm2_sum_axpy_brute_force(seed):
+    rng = np.random.default_rng(50 + seed)
+    n = int(rng.integers(1, 17))
+    x, y = _dyadic(rng, n), _dyadic(rng, n)
+    s2 = sum(Fraction(v) ** 2 for v in x)
+    assert blas.nrm2(x) == math.sqrt(float(s2))             # S exact in FP64, sqrt rounded once
+    assert blas.sum_(x) == float(sum(Fraction(v) for v in x))
+    a = -0.75
+    assert blas.axpy(a, x, y).tolist() == [float(Fraction(a) * Fraction(u) + Fraction(w))
+                                           for u, w in zip(x, y)]
+
+
+def test_axpy_fp32_rounds_twice():
+    # fl(fl(a x) + y): the product is rounded before the add (no fused multiply-add)
+    x = np.array([np.float32(1 + 2 ** -23)], np.float32)
+    y = np.array([np.float32(-1.5)], np.float32)
+    got = blas.axpy(1.5, x, y, mode="f32")[0]
+    prod = np.float32(1.5 * (1 + 2 ** -23))                  # rounds 1.5 + 1.5*2^-23
+    assert got == np.float32(prod + np.float32(-1.5))
+    assert got != np.float32(1.5 * (1 + 2 ** -23) - 1.5)     # the fused value differs
+
+
+def test_nrm2_tolerance_formula():
+    u = 2.0 ** -24
+    assert blas.nrm2_tolerance(1 << 20, 16.0) == (4 * 20 + 2) * u * 4.0

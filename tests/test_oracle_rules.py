@@ -275,3 +275,17 @@ def test_batch_expression_exact_on_integers(n, item, tile, vw):
     e, Lp = ll.batch_reduce("dot", n, item, tile, vw, cast32=False)
     yp = np.concatenate([y, np.zeros(Lp - n)])
     assert evaluate(e, (xp, yp))[0] == x @ y
+
+
+@pytest.mark.parametrize("op", ["nrm2", "sum"])
+@pytest.mark.parametrize("n", [1, 5000, 20000])
+def test_user_function_variant_expressions_exact(op, n):
+    rng = np.random.default_rng(n + 7)
+    x = rng.integers(-50, 50, n).astype(float)
+    e, Lp = ll.reduce_variant(op, n, 1024, 4, 256, 3, True, 1, 256, cast32=False)
+    xp = np.concatenate([x, np.zeros(Lp - n)])
+    got = evaluate(e, xp)[0]
+    if op == "nrm2":
+        assert got == np.sqrt(float((x * x).sum()))
+    else:
+        assert got == x.sum()
