@@ -72,7 +72,8 @@ typedef enum {
   LIFT_OP_NRM2 = 8,
   LIFT_OP_SUM = 9,
   LIFT_OP_AXPY = 10,
-  LIFT_NUM_OPS = 11
+  LIFT_OP_GEMV_T = 11,
+  LIFT_NUM_OPS = 12
 } lift_op;
 
 /* The cost model covers op ids 0 .. LIFT_MLP_OPS-1; the MLP policy falls
@@ -150,6 +151,26 @@ lift_status lift_sum_v(int variant, const float* x, int64_t n, float* result, do
                        void* stream);
 lift_status lift_axpy_v(int variant, int64_t n, float alpha, const float* x, float* y,
                         void* stream);
+
+/* ------------------------------------------------------------------------
+ * gemv-T: y_j <- alpha * sum_i A[i*lda + j] * x_i + beta * y_j, j < N, i < M
+ * (the transposed gemv; x: M floats, y: N floats, read only when beta !=
+ * 0).  In the pattern language the columns of A are the rows of
+ * split^M . reorder-stride^N . join(A) (Sec. 3.2), so this is the Fig. 5
+ * gemv over a reordered matrix.  Each column is folded in fp32 over RB
+ * uniform blocks of rows (the block partials added in order in FP64), then
+ * z_j = fl(alpha * fl32(sum)), y_j = fl(z_j + fl(beta * y_j)).  M == 0 gives
+ * y <- beta * y.  Uses the lift_init workspace (RB * N partial slots and
+ * one counter per column block).
+ * lift_gemv_t_blocks reports the rows per block and the number of blocks a
+ * variant uses for an M x N call.
+ * ------------------------------------------------------------------------ */
+lift_status lift_gemv_t(int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
+                        const float* x, float beta, float* y, void* stream);
+lift_status lift_gemv_t_v(int variant, int64_t M, int64_t N, float alpha, const float* A,
+                          int64_t lda, const float* x, float beta, float* y, void* stream);
+lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_per_block,
+                               int64_t* blocks);
 
 /* ------------------------------------------------------------------------
  * Explicit variants (the autotuner's interface).  `variant` indexes the

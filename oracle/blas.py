@@ -27,8 +27,8 @@ import math
 
 import numpy as np
 
-from .patterns import (C, Join, Map, Reduce, Zip, ZipWith, abs_, add, evaluate,
-                       mult, mult_by, sqrt64, square)
+from .patterns import (C, Join, Map, Reduce, ReorderStride, Split, Zip, ZipWith, abs_,
+                       add, evaluate, mult, mult_by, sqrt64, square)
 
 U_FP32 = 2.0 ** -24
 
@@ -75,6 +75,29 @@ def sum_expr():
 def axpy_expr():
     """Applied to the pair (scal(a, x), y)."""
     return C(Map(add), Zip())
+
+
+def transpose_expr(M: int, N: int):
+    """The columns of a row-major M x N matrix as rows: split^M .
+    reorder-stride^N . join (Sec. 3.2: out[i] = in[i/n + s*(i mod n)] with
+    s = N, n = M reads element (i mod M, i / M))."""
+    return C(Split(M), ReorderStride(s=N), Join())
+
+
+def gemv_t(A, x, y, alpha, beta, mode="f64"):
+    """y' = alpha * A^T x + beta * y: the gemv program over the transposed
+    view of A (x has M entries, y has N)."""
+    A, x, y = np.asarray(A), np.asarray(x), np.asarray(y)
+    M, N = A.shape
+    if N == 0:
+        return np.zeros(0)
+    if M == 0:
+        z = np.zeros(N)
+    else:
+        z = evaluate(C(gemv_z_expr(alpha), transpose_expr(M, N)), A, mode, env={"x": x})
+    if beta == 0:
+        return np.asarray(z, dtype=np.float64)
+    return evaluate(gemv_y_expr(), (z, scal(beta, y, mode)), mode)
 
 
 def nrm2(x, mode="f64") -> float:

@@ -232,3 +232,13 @@ def gemv_z_variant(M: int, N: int, alpha, vw: int, lanes: int = WARP,
     row = gemv_row_variant(N, vw, lanes)
     return C(Map(mult_by(alpha)), Join(), Join(),
              MapWorkgroup(Map(row)), Split(rows_per_cta))
+
+
+def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int):
+    """z of the gemv-T kernel: every column of A (the rows of the
+    reorder-stride view) zipped with x, padded to RB*B, folded in RB blocks
+    of B rows (fp32), the block partials added in order in FP64, rounded to
+    fp32 and multiplied by alpha."""
+    col = C(Map(to_f32), ReduceSeq(add64, 0), Map(to_f64), Join(),
+            Map(ReduceSeq(fold(add, mult), 0)), Split(B), PadTo(RB * B), ZipWith("x"))
+    return C(Map(mult_by(alpha)), Join(), Map(col), Split(M), ReorderStride(s=N), Join())

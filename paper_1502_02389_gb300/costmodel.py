@@ -223,15 +223,17 @@ def main():
     import argparse
     import json
     ap = argparse.ArgumentParser(description="train the variant cost model on the GPU")
-    ap.add_argument("--train", default=os.path.join(DATA, "timings_gb300_train.csv"))
-    ap.add_argument("--heldout", default=os.path.join(DATA, "timings_gb300_heldout.csv"))
+    ap.add_argument("--train", nargs="+", default=[os.path.join(DATA, "timings_gb300_train.csv")])
+    ap.add_argument("--heldout", nargs="+",
+                    default=[os.path.join(DATA, "timings_gb300_heldout.csv")])
     ap.add_argument("--out", required=True)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
     lift.lift_init()
-    tr, ho = tune.load_csv(a.train), tune.load_csv(a.heldout)
+    tr = [r for f in a.train for r in tune.load_csv(f)]
+    ho = [r for f in a.heldout for r in tune.load_csv(f)]
     _, X, T, M = dataset(tr)
     trainer = Trainer(X, T, M, seed=a.seed)
     hist = trainer.train(a.steps, a.lr, log_every=max(1, a.steps // 10))

@@ -35,7 +35,8 @@ lift_status cuda_check(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 static std::mutex g_mu;
 static std::map<int, DeviceState*> g_states;
-constexpr int64_t kPartialCapacity = 1 << 14;
+constexpr int64_t kPartialCapacity = 1 << 22;   // fp32 partial slots (16 MiB)
+extern const int kTicketSlots = 64 + 65536;     // counters: reductions, then gemv-T column blocks
 
 DeviceState* current_state() {
   int dev = -1;
@@ -64,9 +65,11 @@ static lift_status init_device(int device) {
   if (rc == LIFT_OK)
     rc = cuda_check(cudaMalloc(&st->ws.partials64, 2 * kPartialCapacity * sizeof(double)),
                     "workspace");
-  if (rc == LIFT_OK) rc = cuda_check(cudaMalloc(&st->ws.tickets, 64 * sizeof(unsigned)), "workspace");
+  if (rc == LIFT_OK)
+    rc = cuda_check(cudaMalloc(&st->ws.tickets, kTicketSlots * sizeof(unsigned)), "workspace");
   if (rc == LIFT_OK) rc = cuda_check(cudaMalloc(&st->ws.status, sizeof(int)), "workspace");
-  if (rc == LIFT_OK) rc = cuda_check(cudaMemset(st->ws.tickets, 0, 64 * sizeof(unsigned)), "memset");
+  if (rc == LIFT_OK)
+    rc = cuda_check(cudaMemset(st->ws.tickets, 0, kTicketSlots * sizeof(unsigned)), "memset");
   if (rc == LIFT_OK) rc = cuda_check(cudaMemset(st->ws.status, 0, sizeof(int)), "memset");
   if (rc == LIFT_OK) rc = cuda_check(cudaDeviceSynchronize(), "init sync");
   st->ws.capacity = kPartialCapacity;
@@ -94,6 +97,9 @@ void register_gemv_tma(std::vector<Variant>& gemv);   // gemv_tma.cu
 void register_reduce_f32(std::vector<Variant>& asum, std::vector<Variant>& dot,
                          std::vector<Variant>& nrm2, std::vector<Variant>& sum);  // reduce_f32.cu
 void register_axpy(std::vector<Variant>& axpy);       // scal_gemv.cu
+void register_gemv_t(std::vector<Variant>& gemv_t);   // gemv_t.cu
+void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB);
+lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s);
 
 static std::vector<Variant> g_ops[LIFT_NUM_OPS];
 static std::once_flag g_reg_once;
@@ -106,6 +112,7 @@ static void build_registry() {
   register_gemv_tma(g_ops[LIFT_OP_GEMV]);
   register_mixed(g_ops);
   register_axpy(g_ops[LIFT_OP_AXPY]);
+  register_gemv_t(g_ops[LIFT_OP_GEMV_T]);
 }
 
 std::vector<Variant>& registry(int op) {
@@ -173,7 +180,7 @@ struct Mlp {
 };
 
 static int g_policy = LIFT_POLICY_FIXED;
-static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 static std::vector<TableEntry> g_table[LIFT_NUM_OPS];
 static Mlp g_mlp;
 static std::mutex g_policy_mu;
@@ -184,7 +191,7 @@ static std::mutex g_policy_mu;
 static const char* kDefaultName[LIFT_NUM_OPS] = {
     "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t1024_v4_ldg", "gemv_tma_w8_c1024_s3",
     "asum_bf16_t256_u4",    "dot_bf16_t256_u8",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4",
-    "nrm2_t4096_v4_ldg_p1", "sum_t4096_v4_ldg_p1", "axpy_t1024_v4_ldg"};
+    "nrm2_t4096_v4_ldg_p1", "sum_t4096_v4_ldg_p1", "axpy_t1024_v4_ldg", "gemv_t_t256_v4_u8"};
 
 static int find_variant(int op, const char* name) {
   auto& L = registry(op);
@@ -295,7 +302,7 @@ static lift_status resolve(int op, int variant, const Args& a, const Variant** o
   const Variant* v = &L[variant];
   const int al = v->align_bytes;
   bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
-  if (op == LIFT_OP_GEMV) ok = ok && ((a.lda * 4) % al == 0);
+  if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) ok = ok && ((a.lda * 4) % al == 0);
   // bulk copies move whole 16-byte granules of each row
   if (op == LIFT_OP_GEMV && v->info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
   if (!ok && v->fallback >= 0) v = &L[v->fallback];
@@ -540,6 +547,46 @@ lift_status lift_axpy_v(int variant, int64_t n, float alpha, const float* x, flo
   a.n = n;
   a.alpha = alpha;
   return run(LIFT_OP_AXPY, variant, a, stream);
+}
+
+lift_status lift_gemv_t_v(int variant, int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
+                          const float* x, float beta, float* y, void* stream) {
+  if (M < 0 || N < 0 || lda < N || lda < 0) return set_error(LIFT_ERR_INVALID_ARG, "gemv_t sizes");
+  if (N > 0 && !y) return set_error(LIFT_ERR_INVALID_ARG, "gemv_t y is NULL");
+  if (M > 0 && N > 0 && (!A || !x)) return set_error(LIFT_ERR_INVALID_ARG, "gemv_t A/x is NULL");
+  if (!aligned(A, 4) || !aligned(x, 4) || !aligned(y, 4))
+    return set_error(LIFT_ERR_INVALID_ARG, "gemv_t pointers not 4-byte aligned");
+  if (!current_state()) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  if (M == 0) return gemv_t_empty_rows(N, beta, y, static_cast<cudaStream_t>(stream));
+  Args a;
+  a.A = A;
+  a.x = x;
+  a.out = y;
+  a.M = M;
+  a.N = N;
+  a.lda = lda;
+  a.n = M;
+  a.alpha = alpha;
+  a.beta = beta;
+  return run(LIFT_OP_GEMV_T, variant, a, stream);
+}
+
+lift_status lift_gemv_t(int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
+                        const float* x, float beta, float* y, void* stream) {
+  return lift_gemv_t_v(-1, M, N, alpha, A, lda, x, beta, y, stream);
+}
+
+lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_per_block,
+                               int64_t* blocks) {
+  if (variant < 0 || variant >= (int)registry(LIFT_OP_GEMV_T).size() || M < 1 || N < 1 ||
+      !rows_per_block || !blocks)
+    return set_error(LIFT_ERR_INVALID_ARG, "gemv_t_blocks arguments");
+  if (!current_state()) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  Args a;
+  a.M = M;
+  a.N = N;
+  gemv_t_shape(variant, a, rows_per_block, blocks);
+  return LIFT_OK;
 }
 
 lift_status lift_nrm2(const float* x, int64_t n, float* result, void* stream) {

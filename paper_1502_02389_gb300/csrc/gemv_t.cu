@@ -1,0 +1,204 @@
+// gemv-T: y <- alpha * A^T x + beta * y for a row-major M x N matrix A
+// (x: M floats, y: N floats).
+//
+// In the pattern language the transpose is an index function: the columns
+// of A are the rows of  split^M . reorder-stride^N . join (A)  (Sec. 3.2,
+// "Reorder-stride"), so gemv-T is the Fig. 5 gemv over that reordered
+// matrix:  z_j = alpha * dot(col_j, x),  y'_j = z_j + beta * y_j.
+// The kernel evaluates, per column j,
+//
+//   map(mult(alpha)) . map(to_f32) . reduce-seq(add64) . map(to_f64) . join
+//     . map(reduce-seq(lambda acc,(a,b): acc + a*b, 0)) . split^B
+//     . pad-(RB*B) . zip(col_j, x)
+//
+// i.e. the column is split into RB uniform blocks of B rows (the last one
+// padded with zeros); CTA (cb, rb) folds the rows of block rb in order for
+// its THREADS*VW consecutive columns (thread t owns VW adjacent columns, so
+// a warp reads 32*VW*4 contiguous bytes of every row), writes one fp32
+// partial per column, and the last CTA of a column block (an atomic ticket
+// per column block) adds the RB partials of each column in block order in
+// FP64, rounds to fp32, multiplies by alpha and adds fl(beta * y_j) (y is not
+// read when beta == 0).
+#include "lift_internal.cuh"
+
+namespace lift {
+
+extern const int kTicketSlots;     // counters in the workspace (api.cu)
+
+namespace {
+
+template <int THREADS, int VW, int U>
+__global__ void __launch_bounds__(THREADS)
+    gemv_t_kernel(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
+                  const float* __restrict__ x, float beta, float* __restrict__ y, int64_t B,
+                  float* __restrict__ partials, unsigned* __restrict__ tickets) {
+  constexpr int CB = THREADS * VW;
+  const int64_t cb = blockIdx.x, rb = blockIdx.y, RB = gridDim.y;
+  const int64_t c0 = cb * CB + (int64_t)threadIdx.x * VW;
+  const int64_t r0 = rb * B, r1 = (r0 + B < M) ? r0 + B : M;
+  float acc[VW];
+#pragma unroll
+  for (int l = 0; l < VW; ++l) acc[l] = 0.f;
+  const bool full_cols = c0 + VW <= N;
+  int64_t i = r0;
+  if (full_cols) {
+    for (; i + U <= r1; i += U) {
+      Vec<VW> a[U];
+      float xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        ld_stream(A + (i + u) * lda + c0, a[u]);
+        xv[u] = __ldg(x + i + u);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < VW; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a[u].v[l], xv[u]));
+    }
+    for (; i < r1; ++i) {
+      Vec<VW> a;
+      ld_stream(A + i * lda + c0, a);
+      const float xv = __ldg(x + i);
+#pragma unroll
+      for (int l = 0; l < VW; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a.v[l], xv));
+    }
+  } else {
+    for (; i < r1; ++i) {
+      const float xv = __ldg(x + i);
+#pragma unroll
+      for (int l = 0; l < VW; ++l)
+        if (c0 + l < N) acc[l] = __fadd_rn(acc[l], __fmul_rn(__ldg(A + i * lda + c0 + l), xv));
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < VW; ++l)
+    if (c0 + l < N) partials[rb * N + c0 + l] = acc[l];
+
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(tickets + cb, 1u) == static_cast<unsigned>(RB - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+#pragma unroll
+  for (int l = 0; l < VW; ++l) {
+    const int64_t j = c0 + l;
+    if (j >= N) continue;
+    double s = 0.0;
+    for (int64_t q = 0; q < RB; ++q) s = __dadd_rn(s, (double)__ldcg(partials + q * N + j));
+    const float z = __fmul_rn(alpha, static_cast<float>(s));
+    y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
+  }
+  if (threadIdx.x == 0) tickets[cb] = 0u;   // ready for the next call
+}
+
+constexpr int kTicketBase = 64;    // gemv-T tickets follow the reductions' counters
+
+template <int THREADS, int VW, int U>
+struct GemvT {
+  static const void* kernel() { return reinterpret_cast<const void*>(&gemv_t_kernel<THREADS, VW, U>); }
+  // (column blocks, row blocks, rows per block): enough CTAs for one wave of
+  // the persistent size, within the partials workspace
+  static void shape(const Args& a, int64_t& ncb, int64_t& RB, int64_t& B) {
+    constexpr int CB = THREADS * VW;
+    ncb = (a.N + CB - 1) / CB;
+    const int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
+    int64_t want = g > ncb ? (g + ncb - 1) / ncb : 1;
+    DeviceState* st = current_state();
+    const int64_t cap = st ? st->ws.capacity / (a.N > 0 ? a.N : 1) : 1;
+    if (want > cap) want = cap;
+    if (want > a.M) want = a.M;
+    if (want < 1) want = 1;
+    B = (a.M + want - 1) / want;
+    RB = (a.M + B - 1) / B;
+  }
+  static int64_t grid(const Variant&, const Args& a) {
+    int64_t ncb, RB, B;
+    shape(a, ncb, RB, B);
+    return ncb * RB;
+  }
+  static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
+    DeviceState* st = current_state();
+    if (a.N == 0) return LIFT_OK;
+    if (a.M == 0) return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t with M == 0 goes through gemv_t_scale");
+    int64_t ncb, RB, B;
+    shape(a, ncb, RB, B);
+    if (ncb > kTicketSlots - kTicketBase)
+      return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: more column blocks than tickets");
+    if (RB * a.N > st->ws.capacity)
+      return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: N exceeds the partials workspace");
+    int64_t M = a.M, N = a.N, lda = a.lda;
+    float alpha = a.alpha, beta = a.beta;
+    const float* A = a.A;
+    const float* x = static_cast<const float*>(a.x);
+    float* y = a.out;
+    float* partials = st->ws.partials;
+    unsigned* tickets = st->ws.tickets + kTicketBase;
+    void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
+    return launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
+  }
+};
+
+// M == 0: every column's dot is the empty sum, y <- fl(beta * y) (0 if beta == 0)
+__global__ void gemv_t_scale(int64_t N, float beta, float* y) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x)
+    y[j] = beta == 0.f ? 0.f : __fadd_rn(0.f, __fmul_rn(beta, y[j]));
+}
+
+template <int THREADS, int VW, int U>
+Variant gemv_t_variant(const char* name) {
+  using K = GemvT<THREADS, VW, U>;
+  Variant v{};
+  v.info.op = LIFT_OP_GEMV_T;
+  v.info.tile = THREADS * VW;
+  v.info.vw = VW;
+  v.info.threads = THREADS;
+  v.info.stride = 1;
+  v.info.cluster = 1;
+  v.info.passes = 1;
+  v.info.rows = U;
+  v.info.lanes = 1;
+  v.info.final_threads = 1;
+  snprintf(v.info.name, sizeof(v.info.name), "gemv_t_%s", name);
+  v.launch = &K::launch;
+  v.grid = &K::grid;
+  v.align_bytes = VW * 4;
+  v.fallback = 0;
+  return v;
+}
+
+}  // namespace
+
+lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s) {
+  if (N == 0) return LIFT_OK;
+  gemv_t_scale<<<64, 256, 0, s>>>(N, beta, y);
+  return cuda_check(cudaGetLastError(), "gemv_t_scale launch");
+}
+
+void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB) {
+  int64_t ncb, rb, b;
+  switch (id) {
+    case 0: GemvT<256, 1, 8>::shape(a, ncb, rb, b); break;
+    case 1: GemvT<256, 4, 4>::shape(a, ncb, rb, b); break;
+    case 2: GemvT<256, 4, 8>::shape(a, ncb, rb, b); break;
+    case 3: GemvT<128, 4, 8>::shape(a, ncb, rb, b); break;
+    default: GemvT<128, 8, 4>::shape(a, ncb, rb, b); break;
+  }
+  *B = b;
+  *RB = rb;
+}
+
+void register_gemv_t(std::vector<Variant>& L) {
+  L.push_back(gemv_t_variant<256, 1, 8>("t256_v1_u8"));
+  L.push_back(gemv_t_variant<256, 4, 4>("t256_v4_u4"));
+  L.push_back(gemv_t_variant<256, 4, 8>("t256_v4_u8"));
+  L.push_back(gemv_t_variant<128, 4, 8>("t128_v4_u8"));
+  L.push_back(gemv_t_variant<128, 8, 4>("t128_v8_u4"));
+  for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
+}
+
+}  // namespace lift

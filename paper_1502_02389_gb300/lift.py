@@ -20,11 +20,11 @@ LIB_PATH = os.path.join(HERE, "liftblas.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NO_MEMORY, ERR_TIMEOUT, ERR_NOT_INITIALIZED = range(7)
 F32, BF16, FP8_E4M3 = 0, 1, 2
 (OP_ASUM, OP_DOT, OP_SCAL, OP_GEMV, OP_ASUM_BF16, OP_DOT_BF16, OP_ASUM_FP8, OP_DOT_FP8, OP_NRM2,
- OP_SUM, OP_AXPY) = range(11)
-NUM_OPS = 11
+ OP_SUM, OP_AXPY, OP_GEMV_T) = range(12)
+NUM_OPS = 12
 MLP_OPS = 8     # op ids the cost model covers
 OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8", "nrm2",
-            "sum", "axpy"]
+            "sum", "axpy", "gemv_t"]
 POLICY_FIXED, POLICY_TABLE, POLICY_MLP = 0, 1, 2
 
 
@@ -79,6 +79,11 @@ _SIGS = {
     "lift_features": ([ctypes.c_int, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "lift_asum_noalloc": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_nrm2": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_gemv_t": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
+    "lift_gemv_t_v": ([ctypes.c_int, _I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P,
+                       _P], ctypes.c_int),
+    "lift_gemv_t_blocks": ([ctypes.c_int, _I64, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+                           ctypes.c_int),
     "lift_sum": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_axpy": ([_I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
     "lift_nrm2_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
@@ -206,6 +211,24 @@ def lift_scal_v(variant, n, alpha, x, y, stream=None):
 def lift_gemv_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
     _check(lib().lift_gemv_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
                              _stream(stream)), "lift_gemv_v")
+
+
+def lift_gemv_t(M, N, alpha, A, lda, x, beta, y, stream=None):
+    _check(lib().lift_gemv_t(M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y), _stream(stream)),
+           "lift_gemv_t")
+
+
+def lift_gemv_t_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
+    _check(lib().lift_gemv_t_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
+                               _stream(stream)), "lift_gemv_t_v")
+
+
+def lift_gemv_t_blocks(variant, M, N):
+    """(rows per block, blocks) of a gemv-T variant for an M x N call."""
+    b, rb = _I64(), _I64()
+    _check(lib().lift_gemv_t_blocks(variant, M, N, ctypes.byref(b), ctypes.byref(rb)),
+           "lift_gemv_t_blocks")
+    return b.value, rb.value
 
 
 def lift_nrm2(x, n, result, stream=None):

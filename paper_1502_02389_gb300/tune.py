@@ -42,6 +42,8 @@ def op_bytes(op: int, n: int, M: int = 0, N: int = 0) -> int:
         return 8 * n
     if op == lift.OP_GEMV:
         return 4 * M * N + 4 * N + 8 * M
+    if op == lift.OP_GEMV_T:
+        return 4 * M * N + 4 * M + 8 * N
     elem = 2 if op in (lift.OP_ASUM_BF16, lift.OP_DOT_BF16) else 1
     scales = 4 * math.ceil(n / 4096) if op in (lift.OP_ASUM_FP8, lift.OP_DOT_FP8) else 0
     k = 2 if op in (lift.OP_DOT_BF16, lift.OP_DOT_FP8) else 1
@@ -130,6 +132,11 @@ class Buffers:
         if op == lift.OP_SCAL:
             x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
             return lambda: lift.lift_scal_v(vid, n, 1.5, x, y)
+        if op == lift.OP_GEMV_T:
+            A = self._slice("x", "f32", r, M * N)
+            y = self._slice("y", "f32", r, N)
+            xv = self._slice("gx", "f32", 0, M)
+            return lambda: lift.lift_gemv_t_v(vid, M, N, 1.0, A, N, xv, 0.5, y)
         if op == lift.OP_GEMV:
             A = self._slice("x", "f32", r, M * N)
             y = self._slice("y", "f32", r, M)
@@ -295,22 +302,25 @@ def workload_shapes() -> List[Tuple[int, int, int, int]]:
          (lift.OP_GEMV, 8192 * 8192, 8192, 8192), (lift.OP_GEMV, 65536 * 1024, 65536, 1024)]
     s += [(op, 1 << 28, 0, 0) for op in MIXED]
     s += [(op, 1 << 26, 0, 0) for op in (lift.OP_NRM2, lift.OP_SUM, lift.OP_AXPY)]
+    s += [(lift.OP_GEMV_T, 8192 * 8192, 8192, 8192), (lift.OP_GEMV_T, 65536 * 1024, 65536, 1024)]
     return s
 
 
 def random_shapes(count: int, seed: int, ops: Optional[List[int]] = None,
-                  lo: int = 8, hi: int = 28) -> List[Tuple[int, int, int, int]]:
+                  lo: int = 8, hi: int = 28,
+                  gemv_range: Tuple[float, float] = (6, 14)) -> List[Tuple[int, int, int, int]]:
     """Shapes for the cost model: op uniform over ``ops``; vector lengths
-    round(2^U(lo, hi)); gemv M, N = round(2^U(6, 14)) with M*N <= 2^28."""
+    round(2^U(lo, hi)); gemv M, N = round(2^U(gemv_range)) with
+    2^8 <= M*N <= 2^28."""
     rng = np.random.default_rng(seed)
     ops = ops or list(range(lift.MLP_OPS))
     out = []
     while len(out) < count:
         op = int(rng.choice(ops))
         if op == lift.OP_GEMV:
-            M = int(round(2 ** rng.uniform(6, 14)))
-            N = int(round(2 ** rng.uniform(6, 14)))
-            if M * N > (1 << 28):
+            M = int(round(2 ** rng.uniform(*gemv_range)))
+            N = int(round(2 ** rng.uniform(*gemv_range)))
+            if M * N > (1 << 28) or M * N < (1 << 8):
                 continue
             out.append((op, M * N, M, N))
         else:
@@ -327,12 +337,16 @@ def main():
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--table", default=None)
     ap.add_argument("--csv", default=None)
+    ap.add_argument("--ops", type=int, nargs="+", default=None,
+                    help="restrict to these op codes")
+    ap.add_argument("--gemv-range", type=float, nargs=2, default=(6, 14),
+                    help="log2 range of gemv M and N for random shapes")
     ap.add_argument("-v", action="store_true")
     a = ap.parse_args()
     if a.preset == "workloads":
-        shapes = workload_shapes()
+        shapes = [s for s in workload_shapes() if a.ops is None or s[0] in a.ops]
     else:
-        shapes = random_shapes(a.count, a.seed)
+        shapes = random_shapes(a.count, a.seed, a.ops, gemv_range=tuple(a.gemv_range))
     sweep(shapes, a.db, reps=a.reps, verbose=a.v)
     if a.table:
         write_table(load_db(a.db), a.table)

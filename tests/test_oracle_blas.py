@@ -165,3 +165,34 @@ def test_axpy_fp32_rounds_twice():
 def test_nrm2_tolerance_formula():
     u = 2.0 ** -24
     assert blas.nrm2_tolerance(1 << 20, 16.0) == (4 * 20 + 2) * u * 4.0
+
+
+def test_gemv_t_closed_forms_and_transpose():
+    M, N = 29, 41
+    y = np.arange(N, dtype=float) - 5
+    # A_ij = i (row index), x = 1: every column sums to M(M-1)/2
+    A = np.repeat(np.arange(M, dtype=float)[:, None], N, axis=1)
+    out = blas.gemv_t(A, np.ones(M), y, 2.0, 0.5)
+    assert np.array_equal(out, 2.0 * M * (M - 1) / 2 + 0.5 * y)
+    # A_ij = j: column j sums to j * sum(x); a non-transposed read would
+    # give the row sums instead
+    A2 = np.repeat(np.arange(N, dtype=float)[None, :], M, axis=0)
+    x = np.arange(M, dtype=float)
+    out = blas.gemv_t(A2, x, y, 1.0, 0.0)
+    assert np.array_equal(out, np.arange(N) * (M * (M - 1) / 2))
+    # the reorder-stride view is the transpose
+    from oracle.patterns import evaluate
+    B = np.arange(M * N, dtype=float).reshape(M, N)
+    assert np.array_equal(evaluate(blas.transpose_expr(M, N), B), B.T)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gemv_t_brute_force(seed):
+    rng = np.random.default_rng(90 + seed)
+    M, N = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+    A, x, y = _dyadic(rng, (M, N)), _dyadic(rng, M), _dyadic(rng, N)
+    out = blas.gemv_t(A, x, y, -1.5, 0.25)
+    exp = [float(Fraction(-3, 2) * sum(Fraction(A[i, j]) * Fraction(x[i]) for i in range(M))
+                 + Fraction(1, 4) * Fraction(y[j])) for j in range(N)]
+    assert out.tolist() == exp
+    assert blas.gemv_t(np.zeros((0, N)), np.zeros(0), y, 1.0, 0.5).tolist() == (0.5 * y).tolist()

@@ -289,3 +289,13 @@ def test_user_function_variant_expressions_exact(op, n):
         assert got == np.sqrt(float((x * x).sum()))
     else:
         assert got == x.sum()
+
+
+@pytest.mark.parametrize("M,N,B", [(1, 1, 1), (37, 20, 8), (64, 33, 64), (100, 7, 3)])
+def test_gemv_t_variant_expression_exact(M, N, B):
+    rng = np.random.default_rng(M * N)
+    A = rng.integers(-9, 9, (M, N)).astype(float)
+    x = rng.integers(-9, 9, M).astype(float)
+    RB = -(-M // B)
+    z = evaluate(ll.gemv_t_z_variant(M, N, 2.0, B, RB), A, env={"x": x})
+    assert np.array_equal(z, 2.0 * (A.T @ x))
