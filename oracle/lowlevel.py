@@ -234,11 +234,20 @@ def gemv_z_variant(M: int, N: int, alpha, vw: int, lanes: int = WARP,
              MapWorkgroup(Map(row)), Split(rows_per_cta))
 
 
-def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int):
+def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int, passes: int = 1):
     """z of the gemv-T kernel: every column of A (the rows of the
     reorder-stride view) zipped with x, padded to RB*B, folded in RB blocks
-    of B rows (fp32), the block partials added in order in FP64, rounded to
-    fp32 and multiplied by alpha."""
-    col = C(Map(to_f32), ReduceSeq(add64, 0), Map(to_f64), Join(),
+    of B rows (fp32); the block partials are then combined in fp32 --
+    one pass: added in block order; two pass: lane l of one warp adds
+    partials l, l+32, ..., then a halving tree over the lanes -- and
+    multiplied by alpha."""
+    if passes == 1:
+        combine = ReduceSeq(add, 0)
+    else:
+        per = max(1, math.ceil(RB / WARP))
+        lanes = C(halving_tree(add), Join(), MapLocal(ReduceSeq(add, 0)), Split(per),
+                  ReorderStride(s=WARP), PadTo(WARP * per))
+        combine = C(Join(), MapWorkgroup(lanes), Split(RB))     # one warp per column
+    col = C(combine, Join(),
             Map(ReduceSeq(fold(add, mult), 0)), Split(B), PadTo(RB * B), ZipWith("x"))
     return C(Map(mult_by(alpha)), Join(), Map(col), Split(M), ReorderStride(s=N), Join())

@@ -5,20 +5,32 @@
 // of A are the rows of  split^M . reorder-stride^N . join (A)  (Sec. 3.2,
 // "Reorder-stride"), so gemv-T is the Fig. 5 gemv over that reordered
 // matrix:  z_j = alpha * dot(col_j, x),  y'_j = z_j + beta * y_j.
-// The kernel evaluates, per column j,
+// The kernels evaluate, per column j,
 //
-//   map(mult(alpha)) . map(to_f32) . reduce-seq(add64) . map(to_f64) . join
+//   map(mult(alpha)) . map(to_f32) . COMBINE . map(to_f64) . join
 //     . map(reduce-seq(lambda acc,(a,b): acc + a*b, 0)) . split^B
 //     . pad-(RB*B) . zip(col_j, x)
 //
 // i.e. the column is split into RB uniform blocks of B rows (the last one
 // padded with zeros); CTA (cb, rb) folds the rows of block rb in order for
 // its THREADS*VW consecutive columns (thread t owns VW adjacent columns, so
-// a warp reads 32*VW*4 contiguous bytes of every row), writes one fp32
-// partial per column, and the last CTA of a column block (an atomic ticket
-// per column block) adds the RB partials of each column in block order in
-// FP64, rounds to fp32, multiplies by alpha and adds fl(beta * y_j) (y is not
-// read when beta == 0).
+// a warp reads 32*VW*4 contiguous bytes of every row) and writes one fp32
+// partial per column.  The two lowerings of COMBINE are a rewrite choice:
+//   one pass:  reduce-seq(add) over the RB partials in block order, done by
+//              the last CTA of each column block (an atomic ticket per
+//              column block); row-major partials P[rb][j];
+//   two pass:  a second kernel, one warp per column: lane l folds partials
+//              l, l+32, ... , then a halving tree over the 32 lanes;
+//              column-major partials P[j][rb] so that a warp's loads are
+//              contiguous.  The second kernel is launched as a programmatic
+//              dependent of the first and waits on it with
+//              griddepcontrol.wait, which hides its launch latency.
+// The combine is fp32: its rounding error (at most ceil(log2 RB) or RB - 1
+// units of fp32 roundoff) is no larger than that of the B-row fold before
+// it, and FP64 arithmetic runs at a small fraction of the fp32 rate on this
+// part, which made an FP64 combine of the N x RB partials cost as much as
+// streaming A.  The epilogue multiplies by alpha and adds fl(beta * y_j) (y
+// is not read when beta == 0).
 #include "lift_internal.cuh"
 
 namespace lift {
@@ -27,7 +39,7 @@ extern const int kTicketSlots;     // counters in the workspace (api.cu)
 
 namespace {
 
-template <int THREADS, int VW, int U>
+template <int THREADS, int VW, int U, int PASSES>
 __global__ void __launch_bounds__(THREADS)
     gemv_t_kernel(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
                   const float* __restrict__ x, float beta, float* __restrict__ y, int64_t B,
@@ -70,6 +82,16 @@ __global__ void __launch_bounds__(THREADS)
         if (c0 + l < N) acc[l] = __fadd_rn(acc[l], __fmul_rn(__ldg(A + i * lda + c0 + l), xv));
     }
   }
+
+  if (PASSES == 2) {
+    // the combine kernel may start launching; it waits for this grid to end
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#pragma unroll
+    for (int l = 0; l < VW; ++l)
+      if (c0 + l < N) partials[(c0 + l) * RB + rb] = acc[l];
+    return;
+  }
+
 #pragma unroll
   for (int l = 0; l < VW; ++l)
     if (c0 + l < N) partials[rb * N + c0 + l] = acc[l];
@@ -87,21 +109,66 @@ __global__ void __launch_bounds__(THREADS)
   for (int l = 0; l < VW; ++l) {
     const int64_t j = c0 + l;
     if (j >= N) continue;
-    double s = 0.0;
-    for (int64_t q = 0; q < RB; ++q) s = __dadd_rn(s, (double)__ldcg(partials + q * N + j));
-    const float z = __fmul_rn(alpha, static_cast<float>(s));
+    float s = 0.f;
+    int64_t q = 0;
+    for (; q + 8 <= RB; q += 8) {        // eight loads in flight, added in order
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldcg(partials + (q + k) * N + j);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s = __fadd_rn(s, v[k]);
+    }
+    for (; q < RB; ++q) s = __fadd_rn(s, __ldcg(partials + q * N + j));
+    const float z = __fmul_rn(alpha, s);
     y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
   }
   if (threadIdx.x == 0) tickets[cb] = 0u;   // ready for the next call
 }
 
+// Second pass: column j's RB partials P[j][0..RB) -> y_j.  Warp w of the
+// grid takes columns w, w + W, ...; lane l folds partials l, l+32, ...
+// (eight loads in flight, added in order), then a halving tree over the
+// lanes (shuffle-down 16, 8, 4, 2, 1).
+__global__ void __launch_bounds__(256)
+    gemv_t_combine(int64_t N, int64_t RB, float alpha, float beta,
+                   const float* __restrict__ partials, float* __restrict__ y) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x / kWarp);
+  for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp; j < N; j += W) {
+    const float* p = partials + j * RB;
+    float s = 0.f;
+    int64_t q = lane;
+    for (; q + 7 * kWarp < RB; q += 8 * kWarp) {
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + q + k * kWarp);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s = __fadd_rn(s, v[k]);
+    }
+    for (; q < RB; q += kWarp) s = __fadd_rn(s, __ldcg(p + q));
+#pragma unroll
+    for (int o = kWarp / 2; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+    if (lane == 0) {
+      const float z = __fmul_rn(alpha, s);
+      y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
+    }
+  }
+}
+
+constexpr int kCombineThreads = 256;
+constexpr int64_t kMaxRowBlocks2 = 512;   // two pass: at most 16 partials per lane
+
 constexpr int kTicketBase = 64;    // gemv-T tickets follow the reductions' counters
 
-template <int THREADS, int VW, int U>
+template <int THREADS, int VW, int U, int PASSES>
 struct GemvT {
-  static const void* kernel() { return reinterpret_cast<const void*>(&gemv_t_kernel<THREADS, VW, U>); }
+  static const void* kernel() {
+    return reinterpret_cast<const void*>(&gemv_t_kernel<THREADS, VW, U, PASSES>);
+  }
   // (column blocks, row blocks, rows per block): enough CTAs for one wave of
-  // the persistent size, within the partials workspace
+  // the persistent size, within the partials workspace (and, two pass, at
+  // most kMaxRowBlocks2 row blocks)
   static void shape(const Args& a, int64_t& ncb, int64_t& RB, int64_t& B) {
     constexpr int CB = THREADS * VW;
     ncb = (a.N + CB - 1) / CB;
@@ -110,6 +177,7 @@ struct GemvT {
     DeviceState* st = current_state();
     const int64_t cap = st ? st->ws.capacity / (a.N > 0 ? a.N : 1) : 1;
     if (want > cap) want = cap;
+    if (PASSES == 2 && want > kMaxRowBlocks2) want = kMaxRowBlocks2;
     if (want > a.M) want = a.M;
     if (want < 1) want = 1;
     B = (a.M + want - 1) / want;
@@ -126,7 +194,7 @@ struct GemvT {
     if (a.M == 0) return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t with M == 0 goes through gemv_t_scale");
     int64_t ncb, RB, B;
     shape(a, ncb, RB, B);
-    if (ncb > kTicketSlots - kTicketBase)
+    if (PASSES == 1 && ncb > kTicketSlots - kTicketBase)
       return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: more column blocks than tickets");
     if (RB * a.N > st->ws.capacity)
       return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: N exceeds the partials workspace");
@@ -138,7 +206,30 @@ struct GemvT {
     float* partials = st->ws.partials;
     unsigned* tickets = st->ws.tickets + kTicketBase;
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
-    return launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
+    lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
+    if (r != LIFT_OK || PASSES == 1) return r;
+    return launch_combine(N, RB, alpha, beta, partials, y, s);
+  }
+  static lift_status launch_combine(int64_t N, int64_t RB, float alpha, float beta,
+                                    const float* partials, float* y, cudaStream_t s) {
+    const void* k = reinterpret_cast<const void*>(&gemv_t_combine);
+    const int64_t per = kCombineThreads / kWarp;
+    int64_t g = (N + per - 1) / per;
+    const int64_t gmax = persistent_grid(k, kCombineThreads, 0, 1);
+    if (g > gmax) g = gmax;
+    if (g < 1) g = 1;
+    void* args[] = {&N, &RB, &alpha, &beta, &partials, &y};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(kCombineThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_check(cudaLaunchKernelExC(&cfg, k, args), "gemv_t combine launch");
   }
 };
 
@@ -149,9 +240,9 @@ __global__ void gemv_t_scale(int64_t N, float beta, float* y) {
     y[j] = beta == 0.f ? 0.f : __fadd_rn(0.f, __fmul_rn(beta, y[j]));
 }
 
-template <int THREADS, int VW, int U>
+template <int THREADS, int VW, int U, int PASSES>
 Variant gemv_t_variant(const char* name) {
-  using K = GemvT<THREADS, VW, U>;
+  using K = GemvT<THREADS, VW, U, PASSES>;
   Variant v{};
   v.info.op = LIFT_OP_GEMV_T;
   v.info.tile = THREADS * VW;
@@ -159,10 +250,10 @@ Variant gemv_t_variant(const char* name) {
   v.info.threads = THREADS;
   v.info.stride = 1;
   v.info.cluster = 1;
-  v.info.passes = 1;
+  v.info.passes = PASSES;
   v.info.rows = U;
   v.info.lanes = 1;
-  v.info.final_threads = 1;
+  v.info.final_threads = PASSES == 2 ? kWarp : 1;
   snprintf(v.info.name, sizeof(v.info.name), "gemv_t_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
@@ -179,25 +270,31 @@ lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s) {
   return cuda_check(cudaGetLastError(), "gemv_t_scale launch");
 }
 
+#define LIFT_GEMV_T_VARIANTS(X)      \
+  X(256, 1, 8, 1, "t256_v1_u8")      \
+  X(128, 4, 8, 1, "t128_v4_u8")      \
+  X(256, 1, 8, 2, "t256_v1_u8_p2")   \
+  X(256, 4, 4, 2, "t256_v4_u4_p2")   \
+  X(256, 4, 8, 2, "t256_v4_u8_p2")   \
+  X(128, 4, 8, 2, "t128_v4_u8_p2")   \
+  X(128, 8, 4, 2, "t128_v8_u4_p2")   \
+  X(64, 4, 8, 2, "t64_v4_u8_p2")
+
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB) {
-  int64_t ncb, rb, b;
-  switch (id) {
-    case 0: GemvT<256, 1, 8>::shape(a, ncb, rb, b); break;
-    case 1: GemvT<256, 4, 4>::shape(a, ncb, rb, b); break;
-    case 2: GemvT<256, 4, 8>::shape(a, ncb, rb, b); break;
-    case 3: GemvT<128, 4, 8>::shape(a, ncb, rb, b); break;
-    default: GemvT<128, 8, 4>::shape(a, ncb, rb, b); break;
-  }
+  int64_t ncb = 0, rb = 0, b = 0;
+  int k = 0;
+#define X(T, V, U, P, NAME) \
+  if (k++ == id) GemvT<T, V, U, P>::shape(a, ncb, rb, b);
+  LIFT_GEMV_T_VARIANTS(X)
+#undef X
   *B = b;
   *RB = rb;
 }
 
 void register_gemv_t(std::vector<Variant>& L) {
-  L.push_back(gemv_t_variant<256, 1, 8>("t256_v1_u8"));
-  L.push_back(gemv_t_variant<256, 4, 4>("t256_v4_u4"));
-  L.push_back(gemv_t_variant<256, 4, 8>("t256_v4_u8"));
-  L.push_back(gemv_t_variant<128, 4, 8>("t128_v4_u8"));
-  L.push_back(gemv_t_variant<128, 8, 4>("t128_v8_u4"));
+#define X(T, V, U, P, NAME) L.push_back(gemv_t_variant<T, V, U, P>(NAME));
+  LIFT_GEMV_T_VARIANTS(X)
+#undef X
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 

@@ -291,11 +291,15 @@ def test_user_function_variant_expressions_exact(op, n):
         assert got == x.sum()
 
 
-@pytest.mark.parametrize("M,N,B", [(1, 1, 1), (37, 20, 8), (64, 33, 64), (100, 7, 3)])
-def test_gemv_t_variant_expression_exact(M, N, B):
+@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("M,N,B", [(1, 1, 1), (37, 20, 8), (64, 33, 64), (100, 7, 3),
+                                   (200, 5, 2)])
+def test_gemv_t_variant_expression_exact(M, N, B, passes):
+    # integer inputs: every operation is exact, so any combine order must
+    # give the exact A^T x (a dropped block, lane or tree level would not)
     rng = np.random.default_rng(M * N)
     A = rng.integers(-9, 9, (M, N)).astype(float)
     x = rng.integers(-9, 9, M).astype(float)
     RB = -(-M // B)
-    z = evaluate(ll.gemv_t_z_variant(M, N, 2.0, B, RB), A, env={"x": x})
+    z = evaluate(ll.gemv_t_z_variant(M, N, 2.0, B, RB, passes), A, env={"x": x})
     assert np.array_equal(z, 2.0 * (A.T @ x))
