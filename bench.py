@@ -43,6 +43,10 @@ WORKLOADS = {
                                   "n=2^28, N(0,1) with 1% x1e3, seed 4"),
     "gemv_square": dict(M=8192, N=8192, desc="gemv fp32 8192x8192, alpha=1, beta=0.5, seed 2"),
     "gemv_tall": dict(M=65536, N=1024, desc="gemv fp32 65536x1024, alpha=1, beta=0.5, seed 2"),
+    "gemv_t_square": dict(M=8192, N=8192, desc="gemv-T (y = A^T x) fp32 8192x8192, alpha=1, "
+                                               "beta=0.5, seed 5"),
+    "gemv_t_tall": dict(M=65536, N=1024, desc="gemv-T (y = A^T x) fp32 65536x1024, alpha=1, "
+                                             "beta=0.5, seed 5"),
     "batch": dict(desc="batched launch: 20,000 ops (asum/dot/gemv, lengths 2^U(8,22), "
                        "gemv M,N 2^U(6,12)), about 60 GB, seed 3, one graph-launched "
                        "persistent kernel"),
@@ -59,7 +63,7 @@ def peaks():
 
 KERNEL_SOURCE = {"asum": "reduce_f32.cu", "dot": "reduce_f32.cu", "scal": "scal_gemv.cu",
                  "gemv": "scal_gemv.cu", "batch": "batch.cu", "mixed": "mixed.cu",
-                 "gemv_tma": "gemv_tma.cu"}
+                 "gemv_tma": "gemv_tma.cu", "gemv_split": "gemv_split.cu", "gemv_t": "gemv_t.cu"}
 
 
 def kernel_hash(tag: str) -> str:
@@ -69,6 +73,10 @@ def kernel_hash(tag: str) -> str:
         op = "mixed"
     elif tag.startswith("gemv_tma"):
         op = "gemv_tma"
+    elif tag.startswith("gemv_split"):
+        op = "gemv_split"
+    elif tag.startswith("gemv_t_"):
+        op = "gemv_t"
     else:
         op = tag.split("_", 1)[0]
     d = os.path.join(ROOT, "paper_1502_02389_gb300", "csrc")
@@ -453,21 +461,28 @@ def run_ours(args, rank, world, dist):
                   "l2": "no flush: every run reads about 60 GB, far beyond the 129 MB L2"}
     else:
         M, N = WORKLOADS[wl]["M"], WORKLOADS[wl]["N"]
-        Ah, xh, yh, a, b = synth.gemv(M, N)
+        trans = wl.startswith("gemv_t")
+        op, opname = (lift.OP_GEMV_T, "gemv_t") if trans else (lift.OP_GEMV, "gemv")
+        call = lift.lift_gemv_t_v if trans else lift.lift_gemv_v
+        Ah, xh, yh, a, b = synth.gemv_t(M, N) if trans else synth.gemv(M, N)
+        nx, ny = (M, N) if trans else (N, M)
         A, xv, y0 = (torch.from_numpy(t).to(dev) for t in (Ah, xh, yh))
         yv = y0.clone()
-        vg = lift.lift_pick(lift.OP_GEMV, M * N, M, N)
-        pg = lift.lift_variant_describe(lift.OP_GEMV, vg)
-        launches_per_step = 1
-        bytes_step = 4 * M * N + 4 * N + 8 * M
-        kg = ["gemv:" + pg["name"], bytes_step, [], []]
+        vg = lift.lift_pick(op, M * N, M, N)
+        pg = lift.lift_variant_describe(op, vg)
+        if trans:
+            launches_per_step = pg["passes"]
+        else:
+            launches_per_step = 1 if lift.lift_gemv_segments(vg, M, N)[1] == 1 else 2
+        bytes_step = 4 * M * N + 4 * nx + 8 * ny
+        kg = [opname + ":" + pg["name"], bytes_step, [], []]
         kernels = [kg]
 
         def step(timed):
             if timed:
                 ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 ev[0].record(s)
-            lift.lift_gemv_v(vg, M, N, float(a), A, N, xv, float(b), yv)
+            call(vg, M, N, float(a), A, N, xv, float(b), yv)
             if timed:
                 ev[1].record(s)
                 kg[2].append(ev[0]); kg[3].append(ev[1])
@@ -476,12 +491,12 @@ def run_ours(args, rank, world, dist):
             A.copy_(Ap, non_blocking=True)
             xv.copy_(xp, non_blocking=True)
             yv.copy_(yp, non_blocking=True)
-            lift.lift_gemv_v(vg, M, N, float(a), A, N, xv, float(b), yv)
+            call(vg, M, N, float(a), A, N, xv, float(b), yv)
             outp.copy_(yv, non_blocking=True)
 
         host = dict(Ap=torch.from_numpy(Ah).pin_memory(), xp=torch.from_numpy(xh).pin_memory(),
-                    yp=torch.from_numpy(yh).pin_memory(), outp=torch.empty(M).pin_memory())
-        h2d, d2h = 4 * M * N + 4 * N + 4 * M, 4 * M
+                    yp=torch.from_numpy(yh).pin_memory(), outp=torch.empty(ny).pin_memory())
+        h2d, d2h = 4 * M * N + 4 * nx + 4 * ny, 4 * ny
         config = {"workload": WORKLOADS[wl]["desc"], "M": M, "N": N, "variants": [pg["name"]],
                   "l2": "no flush: A is 256 MiB, larger than the 129 MB L2"}
 
@@ -631,6 +646,13 @@ def oracle_sample(workload: str, budget_s: float):
         bytes_one = sum(4 * d["M"] * d["N"] + 4 * d["N"] + 8 * d["M"] if d["op"] == synth.GEMV
                         else (8 if d["op"] == synth.DOT else 4) * d["n"] for d in ops)
         what = "first 400 of the 20,000 batch ops (same op/size draws, host values)"
+    elif workload.startswith("gemv_t"):
+        M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
+        A, xv, yv, a, b = synth.gemv_t(M, N)
+        cols = max(1, N // 16)
+        As, ys = np.ascontiguousarray(A[:, :cols]), yv[:cols]
+        work = lambda: blas.gemv_t(As, xv, ys, float(a), float(b))  # noqa: E731
+        bytes_one, what = 4 * M * cols + 4 * M + 8 * cols, f"first {cols} of {N} columns"
     else:
         M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
         A, xv, yv, a, b = synth.gemv(M, N)

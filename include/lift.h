@@ -158,13 +158,29 @@ lift_status lift_axpy_v(int variant, int64_t n, float alpha, const float* x, flo
  * 0).  In the pattern language the columns of A are the rows of
  * split^M . reorder-stride^N . join(A) (Sec. 3.2), so this is the Fig. 5
  * gemv over a reordered matrix.  Each column is folded in fp32 over RB
- * uniform blocks of rows (the block partials added in order in FP64), then
- * z_j = fl(alpha * fl32(sum)), y_j = fl(z_j + fl(beta * y_j)).  M == 0 gives
- * y <- beta * y.  Uses the lift_init workspace (RB * N partial slots and
- * one counter per column block).
+ * uniform blocks of rows; the RB block partials are added in fp32, in block
+ * order (one-pass variants, by the last CTA of each column block) or by a
+ * warp per column, lane l adding partials l, l+32, ... followed by a
+ * halving tree over the lanes (two-pass variants, a second kernel); then
+ * z_j = fl(alpha * sum), y_j = fl(z_j + fl(beta * y_j)).  M == 0 gives
+ * y <- beta * y.  Uses the lift_init workspace (RB * N partial slots and,
+ * one pass, one counter per column block).  Errors: LIFT_ERR_UNSUPPORTED
+ * when RB * N exceeds the workspace.
  * lift_gemv_t_blocks reports the rows per block and the number of blocks a
  * variant uses for an M x N call.
  * ------------------------------------------------------------------------ */
+/* lift_gemv_segments: how a gemv variant splits each row.  The split-row
+ * variants (names "gemv_split_*"; Fig. 3 partial reduction applied to the
+ * row's reduce) give each row *segments CTAs of *seg_len elements (a
+ * multiple of the variant's threads x vector width; the last segment is
+ * ragged) and add the segment partials in fp32 with a warp per row, lane l
+ * adding partials l, l+32, ..., then a halving tree over the lanes; every
+ * other gemv variant reports *seg_len = N, *segments = 1.  Host only; needs
+ * lift_init for the device (the split depends on its SM count).  Errors:
+ * LIFT_ERR_INVALID_ARG for a bad variant, M < 1, N < 0 or NULL outputs. */
+lift_status lift_gemv_segments(int variant, int64_t M, int64_t N, int64_t* seg_len,
+                               int64_t* segments);
+
 lift_status lift_gemv_t(int64_t M, int64_t N, float alpha, const float* A, int64_t lda,
                         const float* x, float beta, float* y, void* stream);
 lift_status lift_gemv_t_v(int variant, int64_t M, int64_t N, float alpha, const float* A,
@@ -244,13 +260,18 @@ lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float*
  *                      autotuner; nearest shape in log2 size).
  *   LIFT_POLICY_MLP:   the cost model (path: weights file written by the
  *                      trainer); argmin of the predicted times.
+ * Both learned policies choose only among the variants that run as
+ * themselves on the call's arguments (vector loads need the pointers and,
+ * for gemv and gemv-T, the row pitch aligned to the vector width); an
+ * explicit or FIXED variant that cannot runs its guarded fallback.
  * ------------------------------------------------------------------------ */
 typedef enum { LIFT_POLICY_FIXED = 0, LIFT_POLICY_TABLE = 1, LIFT_POLICY_MLP = 2 } lift_policy;
 
 lift_status lift_set_policy(int policy, const char* path);
 /* Force `variant` for `op` (-1 clears the override). */
 lift_status lift_set_variant(int op, int variant);
-/* The variant the current policy would use. M, N: gemv shape (else 0). */
+/* The variant the current policy would use for a dense call (aligned
+ * pointers, lda = N).  M, N: gemv / gemv-T shape (else 0). */
 lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
 
 /* The 10 cost-model features of a call, written to out[0..9]: one-hot op

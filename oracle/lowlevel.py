@@ -234,6 +234,32 @@ def gemv_z_variant(M: int, N: int, alpha, vw: int, lanes: int = WARP,
              MapWorkgroup(Map(row)), Split(rows_per_cta))
 
 
+def gemv_split_z_variant(M: int, N: int, alpha, vw: int, threads: int, L: int, S: int):
+    """z of the split-row gemv: each row zipped with x, padded to S*L and
+    split into S segments of L elements; a CTA of ``threads`` folds a
+    segment (thread t takes vectors t, t+threads, ... in order, adds its vw
+    lanes, then ``block_tree``); the S segment partials of the row are added
+    by one warp (lane l takes partials l, l+32, ..., then a halving tree)
+    and multiplied by alpha -- the partial-reduction rule of Fig. 3 applied
+    to each row's reduce."""
+    chunk = threads * vw
+    assert L % chunk == 0 and S * L >= N
+    J = L // chunk
+    f = fold(add, mult)
+    fr = Vect(vw, f) if vw > 1 else f
+    lane_sum = Id()
+    if vw > 1:
+        lane_sum = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
+    segment = C(block_tree(threads), lane_sum, Join(), MapLocal(ReduceSeq(fr, 0)),
+                Split(J), ReorderStride(s=threads), AsVector(vw) if vw > 1 else Id())
+    per = max(1, math.ceil(S / WARP))
+    lanes = C(halving_tree(add), Join(), MapLocal(ReduceSeq(add, 0)), Split(per),
+              ReorderStride(s=WARP), PadTo(WARP * per))
+    row = C(Join(), MapWorkgroup(lanes), Split(S), Join(), MapWorkgroup(segment), Split(L),
+            PadTo(S * L), ZipWith("x"))
+    return C(Map(mult_by(alpha)), Join(), Map(row))
+
+
 def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int, passes: int = 1):
     """z of the gemv-T kernel: every column of A (the rows of the
     reorder-stride view) zipped with x, padded to RB*B, folded in RB blocks

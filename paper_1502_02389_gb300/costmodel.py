@@ -54,9 +54,24 @@ def group(records: List[Dict]) -> Dict[Tuple[int, int, int, int], Dict[int, floa
     return g
 
 
+def runs_as_itself(op: int, variant: int, N: int) -> bool:
+    """Whether a variant runs as itself (not its guarded fallback) on a dense
+    call with aligned pointers: gemv and gemv-T rows of N floats must be a
+    whole number of the variant's vectors (and of 16-byte granules for the
+    bulk-copy gemv).  The same test the library's learned picks apply."""
+    if op not in (lift.OP_GEMV, lift.OP_GEMV_T):
+        return True
+    d = lift.lift_variant_describe(op, variant)
+    if (4 * N) % (4 * d["vw"]) != 0:
+        return False
+    return not (op == lift.OP_GEMV and d["stages"] > 0 and (N == 0 or N % 4 != 0))
+
+
 def dataset(records: List[Dict]):
     """Features X [B, 10], targets T [B, V] = log(t_v / t_best), mask M
-    (the output slices follow ``offsets(records)``)."""
+    (the output slices follow ``offsets(records)``).  A timing of a variant
+    that ran its fallback on that shape is masked out: the picks never
+    choose such a variant there."""
     off, V = offsets(records)
     g = group(records)
     keys = sorted(g)
@@ -70,7 +85,7 @@ def dataset(records: List[Dict]):
         best = min(times.values())
         for v, ms in times.items():
             T[i, off[op] + v] = math.log(ms / best)
-            M[i, off[op] + v] = 1.0
+            M[i, off[op] + v] = 1.0 if runs_as_itself(op, v, N) else 0.0
     return keys, X, T, M
 
 

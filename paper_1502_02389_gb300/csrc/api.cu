@@ -99,6 +99,8 @@ void register_reduce_f32(std::vector<Variant>& asum, std::vector<Variant>& dot,
 void register_axpy(std::vector<Variant>& axpy);       // scal_gemv.cu
 void register_gemv_t(std::vector<Variant>& gemv_t);   // gemv_t.cu
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB);
+void register_gemv_split(std::vector<Variant>& gemv);  // gemv_split.cu
+void gemv_split_shape(int k, const Args& a, int64_t* L, int64_t* S);
 lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s);
 
 static std::vector<Variant> g_ops[LIFT_NUM_OPS];
@@ -110,6 +112,7 @@ static void build_registry() {
   register_scal(g_ops[LIFT_OP_SCAL]);
   register_gemv(g_ops[LIFT_OP_GEMV]);
   register_gemv_tma(g_ops[LIFT_OP_GEMV]);
+  register_gemv_split(g_ops[LIFT_OP_GEMV]);
   register_mixed(g_ops);
   register_axpy(g_ops[LIFT_OP_AXPY]);
   register_gemv_t(g_ops[LIFT_OP_GEMV_T]);
@@ -228,10 +231,26 @@ lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out) {
 
 namespace lift {
 
-static int mlp_pick(int op, int64_t n, int64_t M, int64_t N) {
+static bool ptr_ok(const void* p, int bytes) { return p == nullptr || aligned(p, bytes); }
+
+// Whether variant v runs as itself on these arguments: its vector loads need
+// the pointers (and, gemv and gemv-T, the row pitch) aligned to its vector
+// width, and the bulk-copy gemv needs whole 16-byte row granules.  Otherwise
+// the library runs the variant's guarded fallback instead.
+static bool eligible(int op, const Variant& v, const Args& a) {
+  const int al = v.align_bytes;
+  bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
+  if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) ok = ok && ((a.lda * 4) % al == 0);
+  if (op == LIFT_OP_GEMV && v.info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
+  return ok;
+}
+
+// The learned pick: the variant with the smallest predicted time among those
+// that run as themselves on these arguments.
+static int mlp_pick(int op, const Args& a) {
   const Mlp& m = g_mlp;
   float f[10];
-  lift_features(op, n, M, N, f);
+  lift_features(op, a.n, a.M, a.N, f);
   std::vector<float> h1(m.h1), h2(m.h2);
   for (int j = 0; j < m.h1; ++j) {
     float s = m.b1[j];
@@ -246,12 +265,14 @@ static int mlp_pick(int op, int64_t n, int64_t M, int64_t N) {
   // variants the weights know: the file's slice of this op (a registry that
   // grew after training keeps its newer variants out of the pick)
   const int file_cnt = (op + 1 < LIFT_MLP_OPS ? m.offsets[op + 1] : m.V) - m.offsets[op];
-  const int cnt = std::min((int)registry(op).size(), file_cnt);
+  const auto& L = registry(op);
+  const int cnt = std::min((int)L.size(), file_cnt);
   int best = 0;
   float best_t = INFINITY;
   for (int v = 0; v < cnt; ++v) {
     const int o = m.offsets[op] + v;
     if (o >= m.V) break;
+    if (!eligible(op, L[v], a)) continue;
     float s = m.b3[o];
     for (int i = 0; i < m.h2; ++i) s += h2[i] * m.W3[i * m.V + o];
     if (s < best_t) {
@@ -262,14 +283,19 @@ static int mlp_pick(int op, int64_t n, int64_t M, int64_t N) {
   return best;
 }
 
-static int table_pick(int op, int64_t n, int64_t M, int64_t N) {
+// The tuned table: the variant of the nearest tuned shape (log sizes) among
+// the entries whose variant runs as itself on these arguments.
+static int table_pick(int op, const Args& a) {
   const auto& T = g_table[op];
   if (T.empty()) return -1;
+  const int64_t n = a.n, M = a.M, N = a.N;
   const double ln = log2((double)(op == LIFT_OP_GEMV ? M * N : n) + 1.0);
   const double lm = log2((double)M + 1.0), lN = log2((double)N + 1.0);
+  const auto& L = registry(op);
   double best = INFINITY;
   int v = -1;
   for (const auto& e : T) {
+    if (e.variant < 0 || e.variant >= (int)L.size() || !eligible(op, L[e.variant], a)) continue;
     const double d = (e.ln - ln) * (e.ln - ln) + (e.lm - lm) * (e.lm - lm) + (e.lN - lN) * (e.lN - lN);
     if (d < best) {
       best = d;
@@ -279,17 +305,15 @@ static int table_pick(int op, int64_t n, int64_t M, int64_t N) {
   return v;
 }
 
-static int pick_variant(int op, int64_t n, int64_t M, int64_t N) {
+static int pick_variant(int op, const Args& a) {
   std::lock_guard<std::mutex> lk(g_policy_mu);
   if (g_override[op] >= 0) return g_override[op];
   int v = -1;
-  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < LIFT_MLP_OPS) v = mlp_pick(op, n, M, N);
-  if (g_policy == LIFT_POLICY_TABLE) v = table_pick(op, n, M, N);
+  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < LIFT_MLP_OPS) v = mlp_pick(op, a);
+  if (g_policy == LIFT_POLICY_TABLE) v = table_pick(op, a);
   if (v < 0) v = find_variant(op, kDefaultName[op]);
   return v;
 }
-
-static bool ptr_ok(const void* p, int bytes) { return p == nullptr || aligned(p, bytes); }
 
 // Resolve the variant to run: explicit id or policy pick, then the guarded
 // form when a pointer is not aligned for the chosen variant.
@@ -298,14 +322,9 @@ static lift_status resolve(int op, int variant, const Args& a, const Variant** o
   if (L.empty()) return set_error(LIFT_ERR_UNSUPPORTED, "no variants for op");
   if (variant < -1 || variant >= (int)L.size())
     return set_error(LIFT_ERR_INVALID_ARG, "variant id out of range");
-  if (variant < 0) variant = pick_variant(op, a.n, a.M, a.N);
+  if (variant < 0) variant = pick_variant(op, a);
   const Variant* v = &L[variant];
-  const int al = v->align_bytes;
-  bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
-  if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) ok = ok && ((a.lda * 4) % al == 0);
-  // bulk copies move whole 16-byte granules of each row
-  if (op == LIFT_OP_GEMV && v->info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
-  if (!ok && v->fallback >= 0) v = &L[v->fallback];
+  if (!eligible(op, *v, a) && v->fallback >= 0) v = &L[v->fallback];
   *out = v;
   return LIFT_OK;
 }
@@ -589,6 +608,26 @@ lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_
   return LIFT_OK;
 }
 
+lift_status lift_gemv_segments(int variant, int64_t M, int64_t N, int64_t* seg_len,
+                               int64_t* segments) {
+  auto& L = registry(LIFT_OP_GEMV);
+  if (variant < 0 || variant >= (int)L.size() || M < 1 || N < 0 || !seg_len || !segments)
+    return set_error(LIFT_ERR_INVALID_ARG, "gemv_segments arguments");
+  if (!current_state()) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  if (strncmp(L[variant].info.name, "gemv_split_", 11) != 0) {
+    *seg_len = N;
+    *segments = 1;
+    return LIFT_OK;
+  }
+  int first = variant;
+  while (first > 0 && strncmp(L[first - 1].info.name, "gemv_split_", 11) == 0) --first;
+  Args a;
+  a.M = M;
+  a.N = N;
+  gemv_split_shape(variant - first, a, seg_len, segments);
+  return LIFT_OK;
+}
+
 lift_status lift_nrm2(const float* x, int64_t n, float* result, void* stream) {
   return lift_nrm2_v(-1, x, n, result, nullptr, stream);
 }
@@ -694,7 +733,12 @@ lift_status lift_set_policy(int policy, const char* path) {
 lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant) {
   if (op < 0 || op >= LIFT_NUM_OPS || !variant) return LIFT_ERR_INVALID_ARG;
   if (registry(op).empty()) return LIFT_ERR_UNSUPPORTED;
-  *variant = pick_variant(op, n, M, N);
+  Args a;                 // a dense call: lda = N, aligned pointers
+  a.n = n;
+  a.M = M;
+  a.N = N;
+  a.lda = N;
+  *variant = pick_variant(op, a);
   return LIFT_OK;
 }
 

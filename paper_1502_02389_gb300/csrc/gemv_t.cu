@@ -37,6 +37,9 @@ namespace lift {
 
 extern const int kTicketSlots;     // counters in the workspace (api.cu)
 
+lift_status launch_rows_combine(int64_t n, int64_t per, float alpha, float beta,
+                                const float* partials, float* y, cudaStream_t s);
+
 namespace {
 
 template <int THREADS, int VW, int U, int PASSES>
@@ -208,28 +211,7 @@ struct GemvT {
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
     lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
     if (r != LIFT_OK || PASSES == 1) return r;
-    return launch_combine(N, RB, alpha, beta, partials, y, s);
-  }
-  static lift_status launch_combine(int64_t N, int64_t RB, float alpha, float beta,
-                                    const float* partials, float* y, cudaStream_t s) {
-    const void* k = reinterpret_cast<const void*>(&gemv_t_combine);
-    const int64_t per = kCombineThreads / kWarp;
-    int64_t g = (N + per - 1) / per;
-    const int64_t gmax = persistent_grid(k, kCombineThreads, 0, 1);
-    if (g > gmax) g = gmax;
-    if (g < 1) g = 1;
-    void* args[] = {&N, &RB, &alpha, &beta, &partials, &y};
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)g);
-    cfg.blockDim = dim3(kCombineThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cuda_check(cudaLaunchKernelExC(&cfg, k, args), "gemv_t combine launch");
+    return launch_rows_combine(N, RB, alpha, beta, partials, y, s);
   }
 };
 
@@ -263,6 +245,31 @@ Variant gemv_t_variant(const char* name) {
 }
 
 }  // namespace
+
+// The second pass of gemv-T and of the split-row gemv: n outputs, each from
+// `per` consecutive fp32 partials, launched as a programmatic dependent of
+// the kernel before it on the stream.
+lift_status launch_rows_combine(int64_t n, int64_t per, float alpha, float beta,
+                                const float* partials, float* y, cudaStream_t s) {
+  const void* k = reinterpret_cast<const void*>(&gemv_t_combine);
+  const int64_t warps = kCombineThreads / kWarp;
+  int64_t g = (n + warps - 1) / warps;
+  const int64_t gmax = persistent_grid(k, kCombineThreads, 0, 1);
+  if (g > gmax) g = gmax;
+  if (g < 1) g = 1;
+  void* args[] = {&n, &per, &alpha, &beta, &partials, &y};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g);
+  cfg.blockDim = dim3(kCombineThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cuda_check(cudaLaunchKernelExC(&cfg, k, args), "partials combine launch");
+}
 
 lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s) {
   if (N == 0) return LIFT_OK;

@@ -84,6 +84,8 @@ _SIGS = {
                        _P], ctypes.c_int),
     "lift_gemv_t_blocks": ([ctypes.c_int, _I64, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
                            ctypes.c_int),
+    "lift_gemv_segments": ([ctypes.c_int, _I64, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+                           ctypes.c_int),
     "lift_sum": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_axpy": ([_I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
     "lift_nrm2_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
@@ -229,6 +231,15 @@ def lift_gemv_t_blocks(variant, M, N):
     _check(lib().lift_gemv_t_blocks(variant, M, N, ctypes.byref(b), ctypes.byref(rb)),
            "lift_gemv_t_blocks")
     return b.value, rb.value
+
+
+def lift_gemv_segments(variant, M, N):
+    """(segment length, segments per row) of a gemv variant for an M x N
+    call; (N, 1) for the variants that give a row to one warp or CTA."""
+    L, S = _I64(), _I64()
+    _check(lib().lift_gemv_segments(variant, M, N, ctypes.byref(L), ctypes.byref(S)),
+           "lift_gemv_segments")
+    return L.value, S.value
 
 
 def lift_nrm2(x, n, result, stream=None):

@@ -55,6 +55,16 @@ def gemv(M: int, N: int, seed: int = 2):
     return A, x, y, np.float32(1.0), np.float32(0.5)
 
 
+def gemv_t(M: int, N: int, seed: int = 5):
+    """y <- alpha A^T x + beta y inputs: A (M x N), x (M), y (N), all
+    U(-1, 1); alpha = 1, beta = 0.5."""
+    g = generator(seed)
+    x = g.uniform(-1.0, 1.0, M).astype(np.float32)
+    y = g.uniform(-1.0, 1.0, N).astype(np.float32)
+    A = g.uniform(-1.0, 1.0, (M, N)).astype(np.float32)
+    return A, x, y, np.float32(1.0), np.float32(0.5)
+
+
 def mixed_values(n: int = 1 << 28, seed: int = 4, two: bool = True):
     """FP64 draws x (and y) with 1 % of the entries scaled by 1e3."""
     g = generator(seed)

@@ -341,9 +341,14 @@ def main():
                     help="restrict to these op codes")
     ap.add_argument("--gemv-range", type=float, nargs=2, default=(6, 14),
                     help="log2 range of gemv M and N for random shapes")
+    ap.add_argument("--shapes-from", default=None,
+                    help="time the shapes of an existing timing CSV (filtered by --ops)")
     ap.add_argument("-v", action="store_true")
     a = ap.parse_args()
-    if a.preset == "workloads":
+    if a.shapes_from:
+        shapes = sorted({(r["op"], r["n"], r["M"], r["N"]) for r in load_csv(a.shapes_from)
+                         if a.ops is None or r["op"] in a.ops})
+    elif a.preset == "workloads":
         shapes = [s for s in workload_shapes() if a.ops is None or s[0] in a.ops]
     else:
         shapes = random_shapes(a.count, a.seed, a.ops, gemv_range=tuple(a.gemv_range))

@@ -247,7 +247,8 @@ def test_gemv_all_variants_full_size_sampled_rows(L, shape):
         assert not bad.any(), (L.lift_variant_describe(L.OP_GEMV, vid)["name"], np.flatnonzero(bad)[:5])
 
 
-@pytest.mark.parametrize("M,N", [(1, 1), (7, 33), (40, 257), (129, 1000), (33, 4100), (5, 8192)])
+@pytest.mark.parametrize("M,N", [(1, 1), (7, 33), (40, 257), (129, 1000), (33, 4100), (5, 8192),
+                                 (3, 50000), (2, 300004)])
 def test_gemv_bit_exact_to_expression(L, M, N):
     rng = np.random.default_rng(M * N)
     A = rng.standard_normal((M, N)).astype(np.float32)
@@ -258,9 +259,13 @@ def test_gemv_bit_exact_to_expression(L, M, N):
         # rows whose pitch (lda * 4 bytes) is not a multiple of the vector
         # load run the 4-byte form (variant 0)
         runs = v if (4 * N) % (4 * v["vw"]) == 0 else L.lift_variant_describe(L.OP_GEMV, 0)
+        if runs["name"].startswith("gemv_split_"):
+            seg, S = L.lift_gemv_segments(runs["id"], M, N)
+            ze = ll.gemv_split_z_variant(M, N, 1.25, runs["vw"], runs["threads"], seg, S)
+        else:
+            ze = ll.gemv_z_variant(M, N, 1.25, runs["vw"], runs["lanes"], 1)
         for beta in (0.5, 0.0):
-            z = evaluate(ll.gemv_z_variant(M, N, 1.25, runs["vw"], runs["lanes"], 1), A, mode="f32",
-                         env={"x": x})
+            z = evaluate(ze, A, mode="f32", env={"x": x})
             if beta != 0:
                 exp = evaluate(C(Map(add), Zip()), (z, evaluate(Map(mult_by(beta)), y, mode="f32")),
                                mode="f32")

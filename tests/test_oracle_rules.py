@@ -303,3 +303,15 @@ def test_gemv_t_variant_expression_exact(M, N, B, passes):
     RB = -(-M // B)
     z = evaluate(ll.gemv_t_z_variant(M, N, 2.0, B, RB, passes), A, env={"x": x})
     assert np.array_equal(z, 2.0 * (A.T @ x))
+
+
+@pytest.mark.parametrize("M,N,vw,threads,L,S", [(3, 1000, 4, 64, 256, 4), (2, 5, 1, 32, 32, 1),
+                                                 (4, 700, 2, 32, 64, 11), (1, 4200, 1, 64, 64, 66)])
+def test_gemv_split_variant_expression_exact(M, N, vw, threads, L, S):
+    # integer inputs: exact in any order, so the segments, lanes and trees
+    # must together cover every product exactly once
+    rng = np.random.default_rng(N)
+    A = rng.integers(-9, 9, (M, N)).astype(float)
+    x = rng.integers(-9, 9, N).astype(float)
+    z = evaluate(ll.gemv_split_z_variant(M, N, 2.0, vw, threads, L, S), A, env={"x": x})
+    assert np.array_equal(z, 2.0 * (A @ x))
