@@ -43,9 +43,9 @@ WORKLOADS = {
                                   "n=2^28, N(0,1) with 1% x1e3, seed 4"),
     "gemv_square": dict(M=8192, N=8192, desc="gemv fp32 8192x8192, alpha=1, beta=0.5, seed 2"),
     "gemv_tall": dict(M=65536, N=1024, desc="gemv fp32 65536x1024, alpha=1, beta=0.5, seed 2"),
-    "gemv_t_square": dict(M=8192, N=8192, desc="gemv-T (y = A^T x) fp32 8192x8192, alpha=1, "
+    "gemv_t_square": dict(M=8192, N=8192, trans=True, desc="gemv-T (y = A^T x) fp32 8192x8192, alpha=1, "
                                                "beta=0.5, seed 5"),
-    "gemv_t_tall": dict(M=65536, N=1024, desc="gemv-T (y = A^T x) fp32 65536x1024, alpha=1, "
+    "gemv_t_tall": dict(M=65536, N=1024, trans=True, desc="gemv-T (y = A^T x) fp32 65536x1024, alpha=1, "
                                              "beta=0.5, seed 5"),
     "batch": dict(desc="batched launch: 20,000 ops (asum/dot/gemv, lengths 2^U(8,22), "
                        "gemv M,N 2^U(6,12)), about 60 GB, seed 3, one graph-launched "
@@ -140,34 +140,61 @@ def job_rate(bytes_per_rank_step: float, steps: int, world: int, max_ms: float) 
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 100 ms) around and during the timed
+    region.  The sampler is started, and its first sample awaited, before
+    the region opens, so that starting nvidia-smi does not overlap the
+    timed work; the samples taken from just before the region to just after
+    it are summarised (a region shorter than the sampling period is covered
+    by its neighbouring samples)."""
 
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
+        import threading
         self.p = None
+        self.lines = []
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.p = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t0 = time.monotonic()
+        while not self.lines and time.monotonic() - t0 < 10.0 and self.p.poll() is None:
+            time.sleep(0.01)
+        self.t_start = time.monotonic()
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append((time.monotonic(), line))
 
     def stop(self):
         if self.p is None:
             return None
-        time.sleep(0.25)
+        t_end = time.monotonic()
+        while (not any(t > t_end for t, _ in self.lines) and time.monotonic() - t_end < 1.0
+               and self.p.poll() is None):
+            time.sleep(0.01)
         self.p.terminate()
         try:
-            out, _ = self.p.communicate(timeout=5)
+            self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-            out, _ = self.p.communicate()
+            self.p.wait()
+        self.reader.join(timeout=2)
+        stamped = list(self.lines)
+        before = [k for k, (t, _) in enumerate(stamped) if t <= self.t_start]
+        lo = before[-1] if before else 0
+        after = [k for k, (t, _) in enumerate(stamped) if t > t_end]
+        hi = after[0] if after else len(stamped) - 1
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
+        for _, line in stamped[lo:hi + 1]:
             f = [t.strip() for t in line.split(",")]
             if len(f) < 6:
                 continue
@@ -461,7 +488,7 @@ def run_ours(args, rank, world, dist):
                   "l2": "no flush: every run reads about 60 GB, far beyond the 129 MB L2"}
     else:
         M, N = WORKLOADS[wl]["M"], WORKLOADS[wl]["N"]
-        trans = wl.startswith("gemv_t")
+        trans = WORKLOADS[wl].get("trans", False)
         op, opname = (lift.OP_GEMV_T, "gemv_t") if trans else (lift.OP_GEMV, "gemv")
         call = lift.lift_gemv_t_v if trans else lift.lift_gemv_v
         Ah, xh, yh, a, b = synth.gemv_t(M, N) if trans else synth.gemv(M, N)
@@ -500,13 +527,15 @@ def run_ours(args, rank, world, dist):
         config = {"workload": WORKLOADS[wl]["desc"], "M": M, "N": N, "variants": [pg["name"]],
                   "l2": "no flush: A is 256 MiB, larger than the 129 MB L2"}
 
-    # ---- warm-up, then K timed steps bracketed by barrier + synchronize
+    # ---- clock sampler up first (its start-up idles the GPU), then the
+    # warm-up steps right before the K timed steps, which are bracketed by
+    # barrier + synchronize
+    clocks = Clocks(local) if rank == 0 else None
     for _ in range(args.warmup):
         step(False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = Clocks(local) if rank == 0 else None
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(s)
@@ -646,7 +675,7 @@ def oracle_sample(workload: str, budget_s: float):
         bytes_one = sum(4 * d["M"] * d["N"] + 4 * d["N"] + 8 * d["M"] if d["op"] == synth.GEMV
                         else (8 if d["op"] == synth.DOT else 4) * d["n"] for d in ops)
         what = "first 400 of the 20,000 batch ops (same op/size draws, host values)"
-    elif workload.startswith("gemv_t"):
+    elif WORKLOADS[workload].get("trans", False):
         M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
         A, xv, yv, a, b = synth.gemv_t(M, N)
         cols = max(1, N // 16)

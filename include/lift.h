@@ -274,11 +274,15 @@ lift_status lift_set_variant(int op, int variant);
  * pointers, lda = N).  M, N: gemv / gemv-T shape (else 0). */
 lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
 
-/* The 10 cost-model features of a call, written to out[0..9]: one-hot op
- * family (asum, dot, scal, gemv), log2(n+1)/32, log2(M+1)/16,
- * log2(N+1)/16, one-hot element type (fp32, bf16, fp8).  For gemv the
- * size feature uses n = M*N.  Host-only; needs no device.  Defined for op
- * ids below LIFT_MLP_OPS (LIFT_ERR_INVALID_ARG otherwise). */
+/* The LIFT_NUM_FEATURES cost-model features of a call, written to
+ * out[0..11]: one-hot op family (asum, dot, scal, gemv), log2(n+1)/32,
+ * log2(M+1)/16, log2(N+1)/16, one-hot element type (fp32, bf16, fp8), and,
+ * gemv only, whether a dense row holds whole 16-byte and whole 32-byte
+ * vectors (N % 4 == 0, N % 8 == 0; 0 for the other ops).  For gemv the
+ * size feature uses n = M*N.  A weights file with d_in < 12 reads the first
+ * d_in.  Host-only; needs no device.  Defined for op ids below LIFT_MLP_OPS
+ * (LIFT_ERR_INVALID_ARG otherwise). */
+#define LIFT_NUM_FEATURES 12
 lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out);
 
 /* ------------------------------------------------------------------------

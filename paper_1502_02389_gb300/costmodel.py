@@ -25,7 +25,7 @@ import numpy as np
 
 from . import lift, tune
 
-D_IN, H1, H2 = 10, 64, 64
+D_IN, H1, H2 = lift.NUM_FEATURES, 64, 64
 DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 WEIGHTS = os.path.join(DATA, "mlp_gb300.txt")   # trained on the GB300 sweep
 

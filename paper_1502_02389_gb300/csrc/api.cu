@@ -217,13 +217,17 @@ lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out) {
   if (op < 0 || op >= LIFT_MLP_OPS || !out) return LIFT_ERR_INVALID_ARG;
   static const int fam[LIFT_MLP_OPS] = {0, 1, 2, 3, 0, 1, 0, 1};
   static const int dt[LIFT_MLP_OPS] = {0, 0, 0, 0, 1, 1, 2, 2};
-  for (int i = 0; i < 10; ++i) out[i] = 0.f;
+  for (int i = 0; i < LIFT_NUM_FEATURES; ++i) out[i] = 0.f;
   out[fam[op]] = 1.f;
   if (op == LIFT_OP_GEMV) n = M * N;
   out[4] = (float)(log2((double)n + 1.0) / 32.0);
   out[5] = (float)(log2((double)M + 1.0) / 16.0);
   out[6] = (float)(log2((double)N + 1.0) / 16.0);
   out[7 + dt[op]] = 1.f;
+  if (op == LIFT_OP_GEMV) {     // whole 16- and 32-byte vectors per dense row
+    out[10] = N % 4 == 0 ? 1.f : 0.f;
+    out[11] = N % 8 == 0 ? 1.f : 0.f;
+  }
   return LIFT_OK;
 }
 
@@ -249,7 +253,7 @@ static bool eligible(int op, const Variant& v, const Args& a) {
 // that run as themselves on these arguments.
 static int mlp_pick(int op, const Args& a) {
   const Mlp& m = g_mlp;
-  float f[10];
+  float f[LIFT_NUM_FEATURES];
   lift_features(op, a.n, a.M, a.N, f);
   std::vector<float> h1(m.h1), h2(m.h2);
   for (int j = 0; j < m.h1; ++j) {
@@ -709,7 +713,8 @@ lift_status lift_set_policy(int policy, const char* path) {
     Mlp m;
     std::string tag, off;
     int ver;
-    if (!(f >> tag >> ver >> m.d_in >> m.h1 >> m.h2 >> m.V) || tag != "lift-mlp" || m.d_in != 10)
+    if (!(f >> tag >> ver >> m.d_in >> m.h1 >> m.h2 >> m.V) || tag != "lift-mlp" || m.d_in < 1 ||
+        m.d_in > LIFT_NUM_FEATURES)
       return set_error(LIFT_ERR_INVALID_ARG, "bad MLP header");
     if (!(f >> off) || off != "offsets") return set_error(LIFT_ERR_INVALID_ARG, "bad MLP offsets");
     for (int i = 0; i < LIFT_MLP_OPS; ++i) f >> m.offsets[i];

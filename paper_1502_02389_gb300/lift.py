@@ -23,6 +23,7 @@ F32, BF16, FP8_E4M3 = 0, 1, 2
  OP_SUM, OP_AXPY, OP_GEMV_T) = range(12)
 NUM_OPS = 12
 MLP_OPS = 8     # op ids the cost model covers
+NUM_FEATURES = 12   # lift_features output length
 OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8", "nrm2",
             "sum", "axpy", "gemv_t"]
 POLICY_FIXED, POLICY_TABLE, POLICY_MLP = 0, 1, 2
@@ -321,7 +322,7 @@ def lift_pick(op: int, n: int, M: int = 0, N: int = 0) -> int:
 
 
 def lift_features(op: int, n: int, M: int = 0, N: int = 0) -> List[float]:
-    out = (ctypes.c_float * 10)()
+    out = (ctypes.c_float * NUM_FEATURES)()
     _check(lib().lift_features(op, n, M, N, out), "lift_features")
     return list(out)
 

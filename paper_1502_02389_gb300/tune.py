@@ -308,10 +308,11 @@ def workload_shapes() -> List[Tuple[int, int, int, int]]:
 
 def random_shapes(count: int, seed: int, ops: Optional[List[int]] = None,
                   lo: int = 8, hi: int = 28,
-                  gemv_range: Tuple[float, float] = (6, 14)) -> List[Tuple[int, int, int, int]]:
+                  gemv_range: Tuple[float, float] = (6, 14),
+                  align_n: int = 1) -> List[Tuple[int, int, int, int]]:
     """Shapes for the cost model: op uniform over ``ops``; vector lengths
-    round(2^U(lo, hi)); gemv M, N = round(2^U(gemv_range)) with
-    2^8 <= M*N <= 2^28."""
+    round(2^U(lo, hi)); gemv M, N = round(2^U(gemv_range)) (N rounded up to
+    a multiple of ``align_n``) with 2^8 <= M*N <= 2^28."""
     rng = np.random.default_rng(seed)
     ops = ops or list(range(lift.MLP_OPS))
     out = []
@@ -320,6 +321,7 @@ def random_shapes(count: int, seed: int, ops: Optional[List[int]] = None,
         if op == lift.OP_GEMV:
             M = int(round(2 ** rng.uniform(*gemv_range)))
             N = int(round(2 ** rng.uniform(*gemv_range)))
+            N = -(-N // align_n) * align_n
             if M * N > (1 << 28) or M * N < (1 << 8):
                 continue
             out.append((op, M * N, M, N))
@@ -341,6 +343,8 @@ def main():
                     help="restrict to these op codes")
     ap.add_argument("--gemv-range", type=float, nargs=2, default=(6, 14),
                     help="log2 range of gemv M and N for random shapes")
+    ap.add_argument("--align-n", type=int, default=1,
+                    help="round random gemv N up to a multiple of this")
     ap.add_argument("--shapes-from", default=None,
                     help="time the shapes of an existing timing CSV (filtered by --ops)")
     ap.add_argument("-v", action="store_true")
@@ -351,7 +355,8 @@ def main():
     elif a.preset == "workloads":
         shapes = [s for s in workload_shapes() if a.ops is None or s[0] in a.ops]
     else:
-        shapes = random_shapes(a.count, a.seed, a.ops, gemv_range=tuple(a.gemv_range))
+        shapes = random_shapes(a.count, a.seed, a.ops, gemv_range=tuple(a.gemv_range),
+                               align_n=a.align_n)
     sweep(shapes, a.db, reps=a.reps, verbose=a.v)
     if a.table:
         write_table(load_db(a.db), a.table)

@@ -67,14 +67,18 @@ def test_variant_registry_host_side(lib):
 def test_features_follow_their_definition(lib):
     from paper_1502_02389_gb300 import lift
     f = lift.lift_features(lift.OP_DOT, 1 << 20)
-    assert f[:4] == [0, 1, 0, 0] and f[7:] == [1, 0, 0]
+    assert len(f) == lift.NUM_FEATURES
+    assert f[:4] == [0, 1, 0, 0] and f[7:] == [1, 0, 0, 0, 0]
     assert math.isclose(f[4], math.log2(2 ** 20 + 1) / 32, rel_tol=1e-6)
     g = lift.lift_features(lift.OP_GEMV, 0, 4096, 1024)
     assert g[3] == 1 and math.isclose(g[4], math.log2(4096 * 1024 + 1) / 32, rel_tol=1e-6)
     assert math.isclose(g[5], math.log2(4097) / 16, rel_tol=1e-6)
     assert math.isclose(g[6], math.log2(1025) / 16, rel_tol=1e-6)
+    assert g[10:] == [1, 1]                       # 1024 % 4 == 0 and 1024 % 8 == 0
     h = lift.lift_features(lift.OP_ASUM_FP8, 100)
     assert h[0] == 1 and h[9] == 1
+    assert lift.lift_features(lift.OP_GEMV, 0, 10, 96)[10:] == [1, 1]
+    assert lift.lift_features(lift.OP_GEMV, 0, 10, 97)[10:] == [0, 0]
 
 
 def test_invalid_arguments_rejected_before_any_launch(lib):
