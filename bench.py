@@ -47,6 +47,8 @@ WORKLOADS = {
                                                "beta=0.5, seed 5"),
     "gemv_t_tall": dict(M=65536, N=1024, trans=True, desc="gemv-T (y = A^T x) fp32 65536x1024, alpha=1, "
                                              "beta=0.5, seed 5"),
+    "blackscholes": dict(n=1 << 26, desc="BlackScholes map (Fig. 6): 2^26 prices U(5,30), K=20, "
+                                         "r=0.02, sigma=0.3, T=1, seed 6; call + put out"),
     "batch": dict(desc="batched launch: 20,000 ops (asum/dot/gemv, lengths 2^U(8,22), "
                        "gemv M,N 2^U(6,12)), about 60 GB, seed 3, one graph-launched "
                        "persistent kernel"),
@@ -63,7 +65,8 @@ def peaks():
 
 KERNEL_SOURCE = {"asum": "reduce_f32.cu", "dot": "reduce_f32.cu", "scal": "scal_gemv.cu",
                  "gemv": "scal_gemv.cu", "batch": "batch.cu", "mixed": "mixed.cu",
-                 "gemv_tma": "gemv_tma.cu", "gemv_split": "gemv_split.cu", "gemv_t": "gemv_t.cu"}
+                 "gemv_tma": "gemv_tma.cu", "gemv_split": "gemv_split.cu", "gemv_t": "gemv_t.cu",
+                 "blackscholes": "blackscholes.cu"}
 
 
 def kernel_hash(tag: str) -> str:
@@ -416,6 +419,40 @@ def run_ours(args, rank, world, dist):
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
                   "l2": "flushed before every step (a 512 MiB read between the timed spans)"}
         flushed = True
+    elif wl == "blackscholes":
+        n = WORKLOADS[wl]["n"]
+        sh = synth.stock_prices(n)
+        prm = (synth.BS_STRIKE, synth.BS_RATE, synth.BS_VOL, synth.BS_YEARS)
+        sp = torch.from_numpy(sh).to(dev)
+        call, put = torch.empty(n, device=dev), torch.empty(n, device=dev)
+        vb = lift.lift_pick(lift.OP_BLACKSCHOLES, n)
+        pb = lift.lift_variant_describe(lift.OP_BLACKSCHOLES, vb)
+        launches_per_step = 1
+        bytes_step = 12 * n
+        kb = ["blackscholes:" + pb["name"], bytes_step, [], []]
+        kernels = [kb]
+
+        def step(timed):
+            if timed:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(s)
+            lift.lift_blackscholes_v(vb, n, sp, *prm, call, put)
+            if timed:
+                ev[1].record(s)
+                kb[2].append(ev[0]); kb[3].append(ev[1])
+
+        def e2e_step(sp_h, c_h, p_h):
+            sp.copy_(sp_h, non_blocking=True)
+            lift.lift_blackscholes_v(vb, n, sp, *prm, call, put)
+            c_h.copy_(call, non_blocking=True)
+            p_h.copy_(put, non_blocking=True)
+
+        host = dict(sp_h=torch.from_numpy(sh).pin_memory(), c_h=torch.empty(n).pin_memory(),
+                    p_h=torch.empty(n).pin_memory())
+        h2d, d2h = 4 * n, 8 * n
+        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pb["name"]],
+                  "options_per_s_note": "value / 12 bytes per option",
+                  "l2": "no flush: 768 MiB moved per step, far beyond the 129 MB L2"}
     elif wl == "batch":
         from paper_1502_02389_gb300 import costmodel
         ops = synth.batch_ops()[:args.batch_ops]
@@ -652,6 +689,13 @@ def oracle_sample(workload: str, budget_s: float):
         x = synth.asum_small(n)
         work = lambda: blas.asum(x)  # noqa: E731
         bytes_one, what = 4 * n, "full step (asum, n=2^20)"
+    elif workload == "blackscholes":
+        from oracle import finance
+        n = 1 << 22
+        sh = synth.stock_prices(WORKLOADS[workload]["n"])[:n]
+        work = lambda: finance.black_scholes(sh, synth.BS_STRIKE, synth.BS_RATE,  # noqa: E731
+                                             synth.BS_VOL, synth.BS_YEARS)
+        bytes_one, what = 12 * n, "the first 2^22 prices (the paper's problem size)"
     elif workload == "batch":
         ops = synth.batch_ops()[:400]
         rng = np.random.default_rng(3)

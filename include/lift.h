@@ -73,7 +73,8 @@ typedef enum {
   LIFT_OP_SUM = 9,
   LIFT_OP_AXPY = 10,
   LIFT_OP_GEMV_T = 11,
-  LIFT_NUM_OPS = 12
+  LIFT_OP_BLACKSCHOLES = 12,
+  LIFT_NUM_OPS = 13
 } lift_op;
 
 /* The cost model covers op ids 0 .. LIFT_MLP_OPS-1; the MLP policy falls
@@ -187,6 +188,29 @@ lift_status lift_gemv_t_v(int variant, int64_t M, int64_t N, float alpha, const 
                           int64_t lda, const float* x, float beta, float* y, void* stream);
 lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_per_block,
                                int64_t* blocks);
+
+/* ------------------------------------------------------------------------
+ * BlackScholes (Sec. 7 "Mathematical Finance Application", Fig. 6):
+ * blackScholes(s) = map(BSComputation, s), a {call, put} pair per stock
+ * price for European options with strike K, riskless rate r, volatility
+ * sigma and maturity T (years) shared by all prices.  The paper does not
+ * print compD1 / compD2 / compCall / compPut; they are the Black-Scholes
+ * model:
+ *   d1 = (ln(S/K) + (r + sigma^2/2) T) / (sigma sqrt T), d2 = d1 - sigma sqrt T
+ *   call = S N(d1) - K e^{-rT} N(d2),   put = call - S + K e^{-rT}
+ * with N(x) = erfc(-x/sqrt 2)/2, evaluated in fp32 (host-rounded constants
+ * 1/K, (r + sigma^2/2) T, sigma sqrt T, 1/(sigma sqrt T), K e^{-rT}).
+ * s: n prices (> 0 for a finite result; 0 gives call 0, put K e^{-rT});
+ * call, put: n floats each (device), written; none of the three may
+ * overlap.  Errors: LIFT_ERR_INVALID_ARG for n < 0, NULL arrays with n > 0,
+ * or K, sigma, T not positive and finite, or r not finite.  All variants
+ * give bit-identical results.
+ * ------------------------------------------------------------------------ */
+lift_status lift_blackscholes(int64_t n, const float* s, float strike, float rate, float volatility,
+                              float years, float* call, float* put, void* stream);
+lift_status lift_blackscholes_v(int variant, int64_t n, const float* s, float strike, float rate,
+                                float volatility, float years, float* call, float* put,
+                                void* stream);
 
 /* ------------------------------------------------------------------------
  * Explicit variants (the autotuner's interface).  `variant` indexes the

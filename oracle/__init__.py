@@ -19,4 +19,5 @@ lowlevel  -- the printed low-level expressions (Fig. 2b, Fig. 8, Fig. 9) and
 mixed     -- exact decoding of bf16 and fp8-e4m3 stored values and the
              mixed-precision asum/dot definitions.
 mlp       -- FP64 forward, backward and Adam step of the variant cost model.
+finance   -- the BlackScholes map of Fig. 6 (Black-Scholes model, FP64).
 """

@@ -100,6 +100,7 @@ void register_axpy(std::vector<Variant>& axpy);       // scal_gemv.cu
 void register_gemv_t(std::vector<Variant>& gemv_t);   // gemv_t.cu
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB);
 void register_gemv_split(std::vector<Variant>& gemv);  // gemv_split.cu
+void register_blackscholes(std::vector<Variant>& bs);  // blackscholes.cu
 void gemv_split_shape(int k, const Args& a, int64_t* L, int64_t* S);
 lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s);
 
@@ -116,6 +117,7 @@ static void build_registry() {
   register_mixed(g_ops);
   register_axpy(g_ops[LIFT_OP_AXPY]);
   register_gemv_t(g_ops[LIFT_OP_GEMV_T]);
+  register_blackscholes(g_ops[LIFT_OP_BLACKSCHOLES]);
 }
 
 std::vector<Variant>& registry(int op) {
@@ -183,7 +185,7 @@ struct Mlp {
 };
 
 static int g_policy = LIFT_POLICY_FIXED;
-static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 static std::vector<TableEntry> g_table[LIFT_NUM_OPS];
 static Mlp g_mlp;
 static std::mutex g_policy_mu;
@@ -194,7 +196,8 @@ static std::mutex g_policy_mu;
 static const char* kDefaultName[LIFT_NUM_OPS] = {
     "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t1024_v4_ldg", "gemv_tma_w8_c1024_s3",
     "asum_bf16_t256_u4",    "dot_bf16_t256_u8",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4",
-    "nrm2_t4096_v4_ldg_p1", "sum_t4096_v4_ldg_p1", "axpy_t1024_v4_ldg", "gemv_t_t256_v4_u4_p2"};
+    "nrm2_t4096_v4_ldg_p1", "sum_t4096_v4_ldg_p1", "axpy_t1024_v4_ldg", "gemv_t_t256_v4_u4_p2",
+    "blackscholes_t256_v4_u2"};
 
 static int find_variant(int op, const char* name) {
   auto& L = registry(op);
@@ -244,6 +247,7 @@ static bool ptr_ok(const void* p, int bytes) { return p == nullptr || aligned(p,
 static bool eligible(int op, const Variant& v, const Args& a) {
   const int al = v.align_bytes;
   bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
+  if (op == LIFT_OP_BLACKSCHOLES) ok = ok && ptr_ok(a.result, al);   // the put array
   if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) ok = ok && ((a.lda * 4) % al == 0);
   if (op == LIFT_OP_GEMV && v.info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
   return ok;
@@ -610,6 +614,31 @@ lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_
   a.N = N;
   gemv_t_shape(variant, a, rows_per_block, blocks);
   return LIFT_OK;
+}
+
+lift_status lift_blackscholes_v(int variant, int64_t n, const float* s, float strike, float rate,
+                                float volatility, float years, float* call, float* put,
+                                void* stream) {
+  if (n < 0 || (n > 0 && (!s || !call || !put)))
+    return set_error(LIFT_ERR_INVALID_ARG, "blackscholes arrays");
+  if (!(strike > 0.f) || !isfinite(strike) || !(volatility > 0.f) || !isfinite(volatility) ||
+      !(years > 0.f) || !isfinite(years) || !isfinite(rate))
+    return set_error(LIFT_ERR_INVALID_ARG, "blackscholes parameters");
+  if (!aligned(s, 4) || !aligned(call, 4) || !aligned(put, 4))
+    return set_error(LIFT_ERR_INVALID_ARG, "blackscholes pointers not 4-byte aligned");
+  const float params[4] = {strike, rate, volatility, years};
+  Args a;
+  a.n = n;
+  a.x = s;
+  a.out = call;
+  a.result = put;
+  a.xscale = params;      // host block read by the launcher
+  return run(LIFT_OP_BLACKSCHOLES, variant, a, stream);
+}
+
+lift_status lift_blackscholes(int64_t n, const float* s, float strike, float rate, float volatility,
+                              float years, float* call, float* put, void* stream) {
+  return lift_blackscholes_v(-1, n, s, strike, rate, volatility, years, call, put, stream);
 }
 
 lift_status lift_gemv_segments(int variant, int64_t M, int64_t N, int64_t* seg_len,

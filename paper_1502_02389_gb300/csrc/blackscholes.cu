@@ -1,0 +1,139 @@
+// BlackScholes as a pure map (arXiv 1502.02389, Sec. 7 "Mathematical Finance
+// Application", Fig. 6):  blackScholes(s) = map(BSComputation, s), one
+// {call, put} pair per stock price.  The paper leaves compD1, compD2,
+// compCall and compPut out; they are the Black-Scholes model for a European
+// option with strike K, riskless rate r, volatility sigma and maturity T:
+//
+//   d1 = (ln(S/K) + (r + sigma^2/2) T) / (sigma sqrt(T)),  d2 = d1 - sigma sqrt(T)
+//   call = S N(d1) - K e^{-rT} N(d2),  put = call - S + K e^{-rT}
+//
+// with N the standard normal distribution, N(x) = erfc(-x / sqrt(2)) / 2
+// (CUDA's erfcf), and the put taken from put-call parity.  The pair is
+// stored as two arrays (the zip of the map's two outputs).
+//
+// Lowering: the rule map(f) -> asScalar . map(vect^VW(f)) . asVector^VW
+// (Fig. 4e), map-workgroup over tiles of THREADS*U vectors dealt round robin
+// to a persistent grid, map-local over the vectors of a tile.  Every variant
+// applies the same per-element function with explicitly rounded operations
+// (no contraction), so all variants agree bit for bit.
+#include <math.h>
+
+#include "lift_internal.cuh"
+
+namespace lift {
+namespace {
+
+struct BsConst {
+  float inv_k;    // 1 / K
+  float mu;       // (r + sigma^2 / 2) T
+  float inv_sq;   // 1 / (sigma sqrt(T))
+  float sq;       // sigma sqrt(T)
+  float ke;       // K e^{-rT}
+};
+
+constexpr float kRsqrt2 = 0.70710678118654752440f;
+
+__device__ __forceinline__ void bs_option(float S, const BsConst& c, float& call, float& put) {
+  const float d1 = __fmul_rn(__fadd_rn(logf(__fmul_rn(S, c.inv_k)), c.mu), c.inv_sq);
+  const float d2 = __fsub_rn(d1, c.sq);
+  const float n1 = __fmul_rn(0.5f, erfcf(__fmul_rn(-d1, kRsqrt2)));
+  const float n2 = __fmul_rn(0.5f, erfcf(__fmul_rn(-d2, kRsqrt2)));
+  call = __fsub_rn(__fmul_rn(S, n1), __fmul_rn(c.ke, n2));
+  put = __fadd_rn(__fsub_rn(call, S), c.ke);
+}
+
+template <int THREADS, int VW, int U>
+__global__ void __launch_bounds__(THREADS)
+    bs_map(int64_t n, const float* __restrict__ s, float* __restrict__ call,
+           float* __restrict__ put, BsConst c) {
+  const int64_t nv = n / VW;                         // whole vectors
+  const int64_t stride = (int64_t)gridDim.x * THREADS * U;
+  for (int64_t base = (int64_t)blockIdx.x * THREADS * U + threadIdx.x; base < nv; base += stride) {
+    Vec<VW> S[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t v = base + (int64_t)u * THREADS;
+      if (v < nv) ld_stream(s + v * VW, S[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t v = base + (int64_t)u * THREADS;
+      if (v >= nv) continue;
+      Vec<VW> C, P;
+#pragma unroll
+      for (int l = 0; l < VW; ++l) bs_option(S[u].v[l], c, C.v[l], P.v[l]);
+      st_stream(call + v * VW, C);
+      st_stream(put + v * VW, P);
+    }
+  }
+  // the ragged tail (fewer than VW elements), one element per thread of CTA 0
+  if (blockIdx.x == 0) {
+    const int64_t i = nv * VW + threadIdx.x;
+    if (i < n) bs_option(__ldg(s + i), c, call[i], put[i]);
+  }
+}
+
+template <int THREADS, int VW, int U>
+struct BlackScholes {
+  static const void* kernel() { return reinterpret_cast<const void*>(&bs_map<THREADS, VW, U>); }
+  static int64_t grid(const Variant&, const Args& a) {
+    const int64_t per = (int64_t)THREADS * U;
+    const int64_t need = (a.n / VW + per - 1) / per;
+    int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
+    if (need < g) g = need;
+    return g < 1 ? 1 : g;
+  }
+  // Args of this op: x = prices, out = call, result = put, and xscale points
+  // at the host block {K, r, sigma, T}.
+  static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
+    if (a.n == 0) return LIFT_OK;
+    const float* p = a.xscale;
+    const double K = p[0], r = p[1], sig = p[2], T = p[3];
+    BsConst c;
+    c.inv_k = (float)(1.0 / K);
+    c.mu = (float)((r + 0.5 * sig * sig) * T);
+    c.sq = (float)(sig * sqrt(T));
+    c.inv_sq = (float)(1.0 / (sig * sqrt(T)));
+    c.ke = (float)(K * exp(-r * T));
+    int64_t n = a.n;
+    const float* prices = static_cast<const float*>(a.x);
+    float* call = a.out;
+    float* put = a.result;
+    void* args[] = {&n, &prices, &call, &put, &c};
+    return launch_config(kernel(), dim3((unsigned)grid(v, a)), dim3(THREADS), 0, 1, s, args);
+  }
+};
+
+template <int THREADS, int VW, int U>
+Variant bs_variant(const char* name) {
+  using K = BlackScholes<THREADS, VW, U>;
+  Variant v{};
+  v.info.op = LIFT_OP_BLACKSCHOLES;
+  v.info.tile = THREADS * VW * U;
+  v.info.vw = VW;
+  v.info.threads = THREADS;
+  v.info.stride = 1;
+  v.info.cluster = 1;
+  v.info.passes = 1;
+  v.info.rows = U;
+  v.info.lanes = 1;
+  snprintf(v.info.name, sizeof(v.info.name), "blackscholes_%s", name);
+  v.launch = &K::launch;
+  v.grid = &K::grid;
+  v.align_bytes = VW * 4;
+  v.fallback = 0;
+  return v;
+}
+
+}  // namespace
+
+void register_blackscholes(std::vector<Variant>& L) {
+  L.push_back(bs_variant<256, 1, 4>("t256_v1_u4"));
+  L.push_back(bs_variant<256, 4, 1>("t256_v4_u1"));
+  L.push_back(bs_variant<256, 4, 2>("t256_v4_u2"));
+  L.push_back(bs_variant<128, 4, 4>("t128_v4_u4"));
+  L.push_back(bs_variant<256, 8, 1>("t256_v8_u1"));
+  for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
+}
+
+}  // namespace lift

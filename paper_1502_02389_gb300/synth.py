@@ -65,6 +65,16 @@ def gemv_t(M: int, N: int, seed: int = 5):
     return A, x, y, np.float32(1.0), np.float32(0.5)
 
 
+# BlackScholes options (Fig. 6 maps over the stock prices only, so the other
+# model inputs are shared constants)
+BS_STRIKE, BS_RATE, BS_VOL, BS_YEARS = 20.0, 0.02, 0.30, 1.0
+
+
+def stock_prices(n: int, seed: int = 6) -> np.ndarray:
+    """Stock prices U(5, 30)."""
+    return generator(seed).uniform(5.0, 30.0, n).astype(np.float32)
+
+
 def mixed_values(n: int = 1 << 28, seed: int = 4, two: bool = True):
     """FP64 draws x (and y) with 1 % of the entries scaled by 1e3."""
     g = generator(seed)

@@ -34,7 +34,7 @@ def op_bytes(op: int, n: int, M: int = 0, N: int = 0) -> int:
     """Algorithmic bytes one call moves."""
     if op in (lift.OP_ASUM, lift.OP_NRM2, lift.OP_SUM):
         return 4 * n
-    if op == lift.OP_AXPY:
+    if op in (lift.OP_AXPY, lift.OP_BLACKSCHOLES):
         return 12 * n
     if op == lift.OP_DOT:
         return 8 * n
@@ -89,6 +89,8 @@ class Pools:
                 a = t.randn(POOL_BYTES // 4, device="cuda", generator=g)
             elif kind == "bf16":
                 a = t.randn(POOL_BYTES // 2, device="cuda", generator=g).to(t.bfloat16)
+            elif kind == "price":   # stock prices U(5, 30)
+                a = t.rand(POOL_BYTES // 4, device="cuda", generator=g) * 25.0 + 5.0
             elif kind == "u8":   # E4M3 codes below 0x7E: finite values, no NaN
                 a = t.randint(0, 0x7E, (POOL_BYTES,), device="cuda", generator=g, dtype=t.uint8)
             else:                # block scales
@@ -132,6 +134,10 @@ class Buffers:
         if op == lift.OP_SCAL:
             x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
             return lambda: lift.lift_scal_v(vid, n, 1.5, x, y)
+        if op == lift.OP_BLACKSCHOLES:
+            sp = self._slice("price", "price", r, n)
+            c, p = self._slice("y", "f32", r, n), self._slice("x", "f32", r, n)
+            return lambda: lift.lift_blackscholes_v(vid, n, sp, 20.0, 0.02, 0.3, 1.0, c, p)
         if op == lift.OP_GEMV_T:
             A = self._slice("x", "f32", r, M * N)
             y = self._slice("y", "f32", r, N)
@@ -295,14 +301,16 @@ def write_table(records: List[Dict], path: str) -> None:
 # shape sets
 # ---------------------------------------------------------------------------
 def workload_shapes() -> List[Tuple[int, int, int, int]]:
-    """The benchmark configurations (asum 2^20, dot/scal 2^26, the two gemv
-    shapes, the mixed ops at 2^28)."""
+    """The benchmark configurations: asum 2^20, dot / scal / asum 2^26, the
+    two gemv shapes, the mixed ops at 2^28, nrm2 / sum / axpy 2^26, the two
+    gemv-T shapes, BlackScholes at 2^22 (the paper's size) and 2^26."""
     s = [(lift.OP_ASUM, 1 << 20, 0, 0), (lift.OP_DOT, 1 << 26, 0, 0), (lift.OP_SCAL, 1 << 26, 0, 0),
          (lift.OP_ASUM, 1 << 26, 0, 0),
          (lift.OP_GEMV, 8192 * 8192, 8192, 8192), (lift.OP_GEMV, 65536 * 1024, 65536, 1024)]
     s += [(op, 1 << 28, 0, 0) for op in MIXED]
     s += [(op, 1 << 26, 0, 0) for op in (lift.OP_NRM2, lift.OP_SUM, lift.OP_AXPY)]
     s += [(lift.OP_GEMV_T, 8192 * 8192, 8192, 8192), (lift.OP_GEMV_T, 65536 * 1024, 65536, 1024)]
+    s += [(lift.OP_BLACKSCHOLES, 1 << 22, 0, 0), (lift.OP_BLACKSCHOLES, 1 << 26, 0, 0)]
     return s
 
 

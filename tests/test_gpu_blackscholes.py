@@ -1,0 +1,90 @@
+"""BlackScholes map (Fig. 6) on the GPU against the FP64 oracle: every
+option of the 4M-price case within the fp32 bound, all variants bit-identical
+to one another, ragged and misaligned inputs, edge cases."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import finance
+from paper_1502_02389_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+K, R, SIG, T = synth.BS_STRIKE, synth.BS_RATE, synth.BS_VOL, synth.BS_YEARS
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_02389_gb300 import build, lift
+    build.build()
+    torch.cuda.set_device(0)
+    lift.lift_init(0)
+    yield lift
+    torch.cuda.synchronize()
+    assert lift.lift_read_status() == 0
+
+
+def run(L, vid, s, offset=0):
+    n = s.numel() - offset
+    call = torch.full((n + offset,), float("nan"), device="cuda")
+    put = torch.full((n + offset,), float("nan"), device="cuda")
+    L.lift_blackscholes_v(vid, n, s[offset:], K, R, SIG, T, call[offset:], put[offset:])
+    return call[offset:].cpu().numpy(), put[offset:].cpu().numpy()
+
+
+def test_paper_size_every_option_within_bound(L):
+    n = 4 * 1024 * 1024                       # the paper's BlackScholes size (Sec. 7.2)
+    sh = synth.stock_prices(n)
+    c_ref, p_ref = finance.black_scholes(sh, K, R, SIG, T)
+    tol = finance.tolerance(sh, K, R, T)
+    s = torch.from_numpy(sh).cuda()
+    first = None
+    for vid in range(L.lift_variant_count(L.OP_BLACKSCHOLES)):
+        c, p = run(L, vid, s)
+        name = L.lift_variant_describe(L.OP_BLACKSCHOLES, vid)["name"]
+        assert np.all(np.abs(c - c_ref) <= tol), name
+        assert np.all(np.abs(p - p_ref) <= tol), name
+        if first is None:
+            first = (c, p)
+        else:                                  # a map's value does not depend on its lowering
+            assert np.array_equal(c, first[0]) and np.array_equal(p, first[1]), name
+
+
+@pytest.mark.parametrize("n", [1, 3, 7, 1000003])
+def test_ragged_and_misaligned(L, n):
+    sh = synth.stock_prices(n + 1, seed=7)
+    s = torch.from_numpy(sh).cuda()
+    ref = None
+    for vid in range(L.lift_variant_count(L.OP_BLACKSCHOLES)):
+        for off in (0, 1):                     # offset 1: 4-byte aligned only -> guarded form
+            c, p = run(L, vid, s, off)
+            cr, pr = finance.black_scholes(sh[off:], K, R, SIG, T)
+            tol = finance.tolerance(sh[off:], K, R, T)
+            assert np.all(np.abs(c - cr) <= tol) and np.all(np.abs(p - pr) <= tol)
+            if off == 0:
+                if ref is None:
+                    ref = (c, p)
+                assert np.array_equal(c, ref[0]) and np.array_equal(p, ref[1])
+
+
+def test_edge_cases(L):
+    from paper_1502_02389_gb300.lift import LiftError
+    L.lift_blackscholes(0, 0, K, R, SIG, T, 0, 0)             # n = 0: nothing
+    s = torch.tensor([0.0, 20.0 * math.exp(-R * T), 1e6], device="cuda")
+    c = torch.empty(3, device="cuda")
+    p = torch.empty(3, device="cuda")
+    L.lift_blackscholes(3, s, K, R, SIG, T, c, p)
+    c, p = c.cpu().numpy(), p.cpu().numpy()
+    ke = np.float32(K * math.exp(-R * T))
+    assert c[0] == 0.0 and p[0] == ke                        # worthless stock
+    cr, pr = finance.black_scholes(s.cpu().numpy(), K, R, SIG, T)
+    tol = finance.tolerance(s.cpu().numpy(), K, R, T)
+    assert np.all(np.abs(c - cr) <= tol) and np.all(np.abs(p - pr) <= tol)
+    for bad in ((0.0, R, SIG, T), (K, R, 0.0, T), (K, R, SIG, -1.0), (K, float("nan"), SIG, T)):
+        with pytest.raises(LiftError):
+            L.lift_blackscholes(3, s, *bad, torch.empty(3, device="cuda"),
+                                torch.empty(3, device="cuda"))
