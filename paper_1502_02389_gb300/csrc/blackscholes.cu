@@ -7,15 +7,21 @@
 //   d1 = (ln(S/K) + (r + sigma^2/2) T) / (sigma sqrt(T)),  d2 = d1 - sigma sqrt(T)
 //   call = S N(d1) - K e^{-rT} N(d2),  put = call - S + K e^{-rT}
 //
-// with N the standard normal distribution, N(x) = erfc(-x / sqrt(2)) / 2
-// (CUDA's erfcf), and the put taken from put-call parity.  The pair is
-// stored as two arrays (the zip of the map's two outputs).
+// with N the standard normal distribution and the put taken from put-call
+// parity.  The pair is stored as two arrays (the zip of the map's two
+// outputs).  Two evaluations of N are variants of the user function:
+//   CND = 0: N(x) = erfc(-x / sqrt(2)) / 2 with CUDA's erfcf;
+//   CND = 1: the polynomial approximation 26.2.17 of Abramowitz and Stegun,
+//            "Handbook of Mathematical Functions" (1964), after Hastings:
+//            for x >= 0 the upper tail is Z(x) (b1 t + ... + b5 t^5),
+//            t = 1 / (1 + p x), with |error| < 7.5e-8; N(x) is one minus
+//            that tail, and N(-x) the tail itself.
 //
 // Lowering: the rule map(f) -> asScalar . map(vect^VW(f)) . asVector^VW
 // (Fig. 4e), map-workgroup over tiles of THREADS*U vectors dealt round robin
 // to a persistent grid, map-local over the vectors of a tile.  Every variant
-// applies the same per-element function with explicitly rounded operations
-// (no contraction), so all variants agree bit for bit.
+// with the same CND applies the same per-element function with explicitly
+// rounded operations (no contraction), so they agree bit for bit.
 #include <math.h>
 
 #include "lift_internal.cuh"
@@ -31,18 +37,36 @@ struct BsConst {
   float ke;       // K e^{-rT}
 };
 
-constexpr float kRsqrt2 = 0.70710678118654752440f;
+constexpr float kRsqrt2 = 0.70710678118654752440f;      // 1 / sqrt(2)
+constexpr float kRsqrt2Pi = 0.39894228040143267794f;    // 1 / sqrt(2 pi)
 
+template <int CND>
+__device__ __forceinline__ float normal_cdf(float x) {
+  if constexpr (CND == 0) {
+    return __fmul_rn(0.5f, erfcf(__fmul_rn(-x, kRsqrt2)));
+  } else {
+    const float ax = fabsf(x);
+    const float t = __frcp_rn(__fmaf_rn(0.2316419f, ax, 1.0f));
+    const float z = __fmul_rn(kRsqrt2Pi, expf(__fmul_rn(-0.5f, __fmul_rn(ax, ax))));
+    float poly = 1.330274429f;
+    poly = __fmaf_rn(poly, t, -1.821255978f);
+    poly = __fmaf_rn(poly, t, 1.781477937f);
+    poly = __fmaf_rn(poly, t, -0.356563782f);
+    poly = __fmaf_rn(poly, t, 0.319381530f);
+    const float tail = __fmul_rn(z, __fmul_rn(poly, t));
+    return x >= 0.f ? __fsub_rn(1.0f, tail) : tail;
+  }
+}
+
+template <int CND>
 __device__ __forceinline__ void bs_option(float S, const BsConst& c, float& call, float& put) {
   const float d1 = __fmul_rn(__fadd_rn(logf(__fmul_rn(S, c.inv_k)), c.mu), c.inv_sq);
   const float d2 = __fsub_rn(d1, c.sq);
-  const float n1 = __fmul_rn(0.5f, erfcf(__fmul_rn(-d1, kRsqrt2)));
-  const float n2 = __fmul_rn(0.5f, erfcf(__fmul_rn(-d2, kRsqrt2)));
-  call = __fsub_rn(__fmul_rn(S, n1), __fmul_rn(c.ke, n2));
+  call = __fsub_rn(__fmul_rn(S, normal_cdf<CND>(d1)), __fmul_rn(c.ke, normal_cdf<CND>(d2)));
   put = __fadd_rn(__fsub_rn(call, S), c.ke);
 }
 
-template <int THREADS, int VW, int U>
+template <int THREADS, int VW, int U, int CND>
 __global__ void __launch_bounds__(THREADS)
     bs_map(int64_t n, const float* __restrict__ s, float* __restrict__ call,
            float* __restrict__ put, BsConst c) {
@@ -61,7 +85,7 @@ __global__ void __launch_bounds__(THREADS)
       if (v >= nv) continue;
       Vec<VW> C, P;
 #pragma unroll
-      for (int l = 0; l < VW; ++l) bs_option(S[u].v[l], c, C.v[l], P.v[l]);
+      for (int l = 0; l < VW; ++l) bs_option<CND>(S[u].v[l], c, C.v[l], P.v[l]);
       st_stream(call + v * VW, C);
       st_stream(put + v * VW, P);
     }
@@ -69,13 +93,13 @@ __global__ void __launch_bounds__(THREADS)
   // the ragged tail (fewer than VW elements), one element per thread of CTA 0
   if (blockIdx.x == 0) {
     const int64_t i = nv * VW + threadIdx.x;
-    if (i < n) bs_option(__ldg(s + i), c, call[i], put[i]);
+    if (i < n) bs_option<CND>(__ldg(s + i), c, call[i], put[i]);
   }
 }
 
-template <int THREADS, int VW, int U>
+template <int THREADS, int VW, int U, int CND>
 struct BlackScholes {
-  static const void* kernel() { return reinterpret_cast<const void*>(&bs_map<THREADS, VW, U>); }
+  static const void* kernel() { return reinterpret_cast<const void*>(&bs_map<THREADS, VW, U, CND>); }
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t per = (int64_t)THREADS * U;
     const int64_t need = (a.n / VW + per - 1) / per;
@@ -104,9 +128,11 @@ struct BlackScholes {
   }
 };
 
-template <int THREADS, int VW, int U>
+constexpr int kPolyFallback = 5;   // id of the first CND = 1 variant (4-byte loads)
+
+template <int THREADS, int VW, int U, int CND>
 Variant bs_variant(const char* name) {
-  using K = BlackScholes<THREADS, VW, U>;
+  using K = BlackScholes<THREADS, VW, U, CND>;
   Variant v{};
   v.info.op = LIFT_OP_BLACKSCHOLES;
   v.info.tile = THREADS * VW * U;
@@ -120,19 +146,25 @@ Variant bs_variant(const char* name) {
   snprintf(v.info.name, sizeof(v.info.name), "blackscholes_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
+  v.info.tree = CND;      // the normal-distribution evaluation (0 erfcf, 1 A&S 26.2.17)
   v.align_bytes = VW * 4;
-  v.fallback = 0;
+  v.fallback = CND == 0 ? 0 : kPolyFallback;
   return v;
 }
 
 }  // namespace
 
 void register_blackscholes(std::vector<Variant>& L) {
-  L.push_back(bs_variant<256, 1, 4>("t256_v1_u4"));
-  L.push_back(bs_variant<256, 4, 1>("t256_v4_u1"));
-  L.push_back(bs_variant<256, 4, 2>("t256_v4_u2"));
-  L.push_back(bs_variant<128, 4, 4>("t128_v4_u4"));
-  L.push_back(bs_variant<256, 8, 1>("t256_v8_u1"));
+  L.push_back(bs_variant<256, 1, 4, 0>("t256_v1_u4"));
+  L.push_back(bs_variant<256, 4, 1, 0>("t256_v4_u1"));
+  L.push_back(bs_variant<256, 4, 2, 0>("t256_v4_u2"));
+  L.push_back(bs_variant<128, 4, 4, 0>("t128_v4_u4"));
+  L.push_back(bs_variant<256, 8, 1, 0>("t256_v8_u1"));
+  L.push_back(bs_variant<256, 1, 4, 1>("t256_v1_u4_as"));
+  L.push_back(bs_variant<256, 4, 1, 1>("t256_v4_u1_as"));
+  L.push_back(bs_variant<256, 4, 2, 1>("t256_v4_u2_as"));
+  L.push_back(bs_variant<128, 4, 4, 1>("t128_v4_u4_as"));
+  L.push_back(bs_variant<256, 8, 1, 1>("t256_v8_u1_as"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 
