@@ -15,7 +15,15 @@
 //            "Handbook of Mathematical Functions" (1964), after Hastings:
 //            for x >= 0 the upper tail is Z(x) (b1 t + ... + b5 t^5),
 //            t = 1 / (1 + p x), with |error| < 7.5e-8; N(x) is one minus
-//            that tail, and N(-x) the tail itself.
+//            that tail, and N(-x) the tail itself;
+//   CND = 2: the same polynomial with CUDA's fast intrinsics for the
+//            logarithm and the reciprocal (__logf, __fdividef), and one
+//            exponential per option: the model's identity
+//            S phi(d1) = K e^{-rT} phi(d2) gives phi(d2) = phi(d1) S / (K e^{-rT}).
+//            An error in d1 moves the call by S phi(d1) - K e^{-rT} phi(d2) = 0
+//            to first order (d2 is formed from the same d1), so the
+//            logarithm's accuracy barely reaches the prices; the exponential,
+//            which scales the tails directly, stays the accurate expf.
 //
 // Lowering: the rule map(f) -> asScalar . map(vect^VW(f)) . asVector^VW
 // (Fig. 4e), map-workgroup over tiles of THREADS*U vectors dealt round robin
@@ -35,6 +43,7 @@ struct BsConst {
   float inv_sq;   // 1 / (sigma sqrt(T))
   float sq;       // sigma sqrt(T)
   float ke;       // K e^{-rT}
+  float inv_ke;   // 1 / (K e^{-rT})
 };
 
 constexpr float kRsqrt2 = 0.70710678118654752440f;      // 1 / sqrt(2)
@@ -46,8 +55,10 @@ __device__ __forceinline__ float normal_cdf(float x) {
     return __fmul_rn(0.5f, erfcf(__fmul_rn(-x, kRsqrt2)));
   } else {
     const float ax = fabsf(x);
-    const float t = __frcp_rn(__fmaf_rn(0.2316419f, ax, 1.0f));
-    const float z = __fmul_rn(kRsqrt2Pi, expf(__fmul_rn(-0.5f, __fmul_rn(ax, ax))));
+    const float den = __fmaf_rn(0.2316419f, ax, 1.0f);
+    const float arg = __fmul_rn(-0.5f, __fmul_rn(ax, ax));
+    const float t = __frcp_rn(den);
+    const float z = __fmul_rn(kRsqrt2Pi, expf(arg));
     float poly = 1.330274429f;
     poly = __fmaf_rn(poly, t, -1.821255978f);
     poly = __fmaf_rn(poly, t, 1.781477937f);
@@ -58,11 +69,34 @@ __device__ __forceinline__ float normal_cdf(float x) {
   }
 }
 
+// N(x) from the tail polynomial of A&S 26.2.17 and z = phi(x)
+__device__ __forceinline__ float normal_cdf_poly(float x, float z) {
+  const float t = __fdividef(1.0f, __fmaf_rn(0.2316419f, fabsf(x), 1.0f));
+  float poly = 1.330274429f;
+  poly = __fmaf_rn(poly, t, -1.821255978f);
+  poly = __fmaf_rn(poly, t, 1.781477937f);
+  poly = __fmaf_rn(poly, t, -0.356563782f);
+  poly = __fmaf_rn(poly, t, 0.319381530f);
+  const float tail = __fmul_rn(z, __fmul_rn(poly, t));
+  return x >= 0.f ? __fsub_rn(1.0f, tail) : tail;
+}
+
 template <int CND>
 __device__ __forceinline__ void bs_option(float S, const BsConst& c, float& call, float& put) {
-  const float d1 = __fmul_rn(__fadd_rn(logf(__fmul_rn(S, c.inv_k)), c.mu), c.inv_sq);
+  const float q = __fmul_rn(S, c.inv_k);
+  const float d1 = __fmul_rn(__fadd_rn(CND == 2 ? __logf(q) : logf(q), c.mu), c.inv_sq);
   const float d2 = __fsub_rn(d1, c.sq);
-  call = __fsub_rn(__fmul_rn(S, normal_cdf<CND>(d1)), __fmul_rn(c.ke, normal_cdf<CND>(d2)));
+  float n1, n2;
+  if constexpr (CND == 2) {
+    const float z1 = __fmul_rn(kRsqrt2Pi, expf(__fmul_rn(-0.5f, __fmul_rn(d1, d1))));
+    const float z2 = __fmul_rn(__fmul_rn(z1, S), c.inv_ke);
+    n1 = normal_cdf_poly(d1, z1);
+    n2 = normal_cdf_poly(d2, z2);
+  } else {
+    n1 = normal_cdf<CND>(d1);
+    n2 = normal_cdf<CND>(d2);
+  }
+  call = __fsub_rn(__fmul_rn(S, n1), __fmul_rn(c.ke, n2));
   put = __fadd_rn(__fsub_rn(call, S), c.ke);
 }
 
@@ -119,6 +153,7 @@ struct BlackScholes {
     c.sq = (float)(sig * sqrt(T));
     c.inv_sq = (float)(1.0 / (sig * sqrt(T)));
     c.ke = (float)(K * exp(-r * T));
+    c.inv_ke = (float)(1.0 / (K * exp(-r * T)));
     int64_t n = a.n;
     const float* prices = static_cast<const float*>(a.x);
     float* call = a.out;
@@ -128,7 +163,8 @@ struct BlackScholes {
   }
 };
 
-constexpr int kPolyFallback = 5;   // id of the first CND = 1 variant (4-byte loads)
+// per CND, the id of its 4-byte-load variant (the guarded form)
+constexpr int kFallback[3] = {0, 2, 5};
 
 template <int THREADS, int VW, int U, int CND>
 Variant bs_variant(const char* name) {
@@ -146,9 +182,9 @@ Variant bs_variant(const char* name) {
   snprintf(v.info.name, sizeof(v.info.name), "blackscholes_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
-  v.info.tree = CND;      // the normal-distribution evaluation (0 erfcf, 1 A&S 26.2.17)
+  v.info.tree = CND;      // the normal-distribution evaluation (0 erfcf, 1 A&S, 2 A&S fast)
   v.align_bytes = VW * 4;
-  v.fallback = CND == 0 ? 0 : kPolyFallback;
+  v.fallback = kFallback[CND];
   return v;
 }
 
@@ -156,15 +192,15 @@ Variant bs_variant(const char* name) {
 
 void register_blackscholes(std::vector<Variant>& L) {
   L.push_back(bs_variant<256, 1, 4, 0>("t256_v1_u4"));
-  L.push_back(bs_variant<256, 4, 1, 0>("t256_v4_u1"));
   L.push_back(bs_variant<256, 4, 2, 0>("t256_v4_u2"));
-  L.push_back(bs_variant<128, 4, 4, 0>("t128_v4_u4"));
-  L.push_back(bs_variant<256, 8, 1, 0>("t256_v8_u1"));
   L.push_back(bs_variant<256, 1, 4, 1>("t256_v1_u4_as"));
-  L.push_back(bs_variant<256, 4, 1, 1>("t256_v4_u1_as"));
   L.push_back(bs_variant<256, 4, 2, 1>("t256_v4_u2_as"));
-  L.push_back(bs_variant<128, 4, 4, 1>("t128_v4_u4_as"));
   L.push_back(bs_variant<256, 8, 1, 1>("t256_v8_u1_as"));
+  L.push_back(bs_variant<256, 1, 4, 2>("t256_v1_u4_fast"));
+  L.push_back(bs_variant<256, 4, 1, 2>("t256_v4_u1_fast"));
+  L.push_back(bs_variant<256, 4, 2, 2>("t256_v4_u2_fast"));
+  L.push_back(bs_variant<128, 4, 4, 2>("t128_v4_u4_fast"));
+  L.push_back(bs_variant<256, 8, 1, 2>("t256_v8_u1_fast"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 
