@@ -63,7 +63,8 @@ def peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCE = {"asum": "reduce_f32.cu", "dot": "reduce_f32.cu", "scal": "scal_gemv.cu",
+KERNEL_SOURCE = {"asum": "reduce_f32.cuh", "dot": "reduce_f32.cuh", "nrm2": "reduce_f32.cuh",
+                 "sum": "reduce_f32.cuh", "scal": "scal_gemv.cu",
                  "gemv": "scal_gemv.cu", "batch": "batch.cu", "mixed": "mixed.cu",
                  "gemv_tma": "gemv_tma.cu", "gemv_split": "gemv_split.cu", "gemv_t": "gemv_t.cu",
                  "blackscholes": "blackscholes.cu"}

@@ -101,6 +101,7 @@ void register_gemv_t(std::vector<Variant>& gemv_t);   // gemv_t.cu
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB);
 void register_gemv_split(std::vector<Variant>& gemv);  // gemv_split.cu
 void register_blackscholes(std::vector<Variant>& bs);  // blackscholes.cu
+void register_reduce_derived(std::vector<Variant>& asum, std::vector<Variant>& dot);  // reduce_derived.cu
 void gemv_split_shape(int k, const Args& a, int64_t* L, int64_t* S);
 lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s);
 
@@ -110,6 +111,7 @@ static std::once_flag g_reg_once;
 static void build_registry() {
   register_reduce_f32(g_ops[LIFT_OP_ASUM], g_ops[LIFT_OP_DOT], g_ops[LIFT_OP_NRM2],
                       g_ops[LIFT_OP_SUM]);
+  register_reduce_derived(g_ops[LIFT_OP_ASUM], g_ops[LIFT_OP_DOT]);
   register_scal(g_ops[LIFT_OP_SCAL]);
   register_gemv(g_ops[LIFT_OP_GEMV]);
   register_gemv_tma(g_ops[LIFT_OP_GEMV]);

@@ -353,6 +353,10 @@ def main():
                     help="log2 range of gemv M and N for random shapes")
     ap.add_argument("--align-n", type=int, default=1,
                     help="round random gemv N up to a multiple of this")
+    ap.add_argument("--derived", action="store_true",
+                    help="time only the variants a rule derivation reaches (derive.py)")
+    ap.add_argument("--variant-names", nargs="+", default=None,
+                    help="time only variants whose names start with one of these")
     ap.add_argument("--shapes-from", default=None,
                     help="time the shapes of an existing timing CSV (filtered by --ops)")
     ap.add_argument("-v", action="store_true")
@@ -365,7 +369,21 @@ def main():
     else:
         shapes = random_shapes(a.count, a.seed, a.ops, gemv_range=tuple(a.gemv_range),
                                align_n=a.align_n)
-    sweep(shapes, a.db, reps=a.reps, verbose=a.v)
+    variants = None
+    if a.derived or a.variant_names:
+        from . import derive
+        variants = {}
+        for op in sorted({sh[0] for sh in shapes}):
+            ids = list(range(lift.lift_variant_count(op)))
+            if a.derived:
+                name = next((k for k, v in derive.OP_IDS.items() if v == op), None)
+                if name is not None:
+                    ids = derive.derivable_variants(name)
+            if a.variant_names:
+                ids = [v for v in ids if lift.lift_variant_describe(op, v)["name"].startswith(
+                    tuple(a.variant_names))]
+            variants[op] = ids
+    sweep(shapes, a.db, reps=a.reps, variants=variants, verbose=a.v)
     if a.table:
         write_table(load_db(a.db), a.table)
     if a.csv:
