@@ -665,7 +665,7 @@ def report(op: str) -> Dict[str, Any]:
 # implementable two-level-tree, strided, directly loaded forms with work-group
 # sizes the hand-picked list (32 and 256 work-items) leaves out.
 EMIT_THREADS = (128, 512)
-EMIT_TILES = (2048, 4096, 8192)
+EMIT_TILES = (1024, 2048, 4096)
 EMIT_WIDTHS = (4, 8)
 
 

@@ -131,7 +131,7 @@ def test_library_variants_reached_and_not():
     assert all("_c" in n for n in r["library_not_derivable"])   # only cluster stages
     assert len(D.derivable_variants("scal")) == lift.lift_variant_count(lift.OP_SCAL)
     derived = [n for n in r["library_reached"] if n.startswith("asum_d")]
-    assert len(derived) == 11                                   # the emitted sets
+    assert len(derived) == sum(ln.startswith("LIFT_DERIVED(0,") for ln in D.emit_lines())
 
 
 def test_emitted_list_is_current():
