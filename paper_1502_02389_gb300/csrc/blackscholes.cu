@@ -16,14 +16,16 @@
 //            for x >= 0 the upper tail is Z(x) (b1 t + ... + b5 t^5),
 //            t = 1 / (1 + p x), with |error| < 7.5e-8; N(x) is one minus
 //            that tail, and N(-x) the tail itself;
-//   CND = 2: the same polynomial with CUDA's fast intrinsics for the
-//            logarithm and the reciprocal (__logf, __fdividef), and one
+//   CND = 2: the same polynomial on the approximate special-function
+//            instructions (lg2.approx, ex2.approx, rcp.approx), with one
 //            exponential per option: the model's identity
 //            S phi(d1) = K e^{-rT} phi(d2) gives phi(d2) = phi(d1) S / (K e^{-rT}).
-//            An error in d1 moves the call by S phi(d1) - K e^{-rT} phi(d2) = 0
-//            to first order (d2 is formed from the same d1), so the
-//            logarithm's accuracy barely reaches the prices; the exponential,
-//            which scales the tails directly, stays the accurate expf.
+//            d1 = lg2(S/K) (ln 2 / (sigma sqrt T)) + (r + sigma^2/2) T / (sigma sqrt T)
+//            is one fused multiply-add, and phi(d1) = 2^(d1 d1 (-1/(2 ln 2))
+//            + log2(1/sqrt(2 pi))) one more and an ex2.  An error in d1 moves
+//            the call by S phi(d1) - K e^{-rT} phi(d2) = 0 to first order (d2 is
+//            formed from the same d1), so the logarithm's accuracy barely
+//            reaches the prices; the exponential scales tails of at most 0.5.
 //
 // Lowering: the rule map(f) -> asScalar . map(vect^VW(f)) . asVector^VW
 // (Fig. 4e), map-workgroup over tiles of THREADS*U vectors dealt round robin
@@ -44,7 +46,28 @@ struct BsConst {
   float sq;       // sigma sqrt(T)
   float ke;       // K e^{-rT}
   float inv_ke;   // 1 / (K e^{-rT})
+  float ln2_sq;   // ln 2 / (sigma sqrt(T))
+  float mu_sq;    // (r + sigma^2 / 2) T / (sigma sqrt(T))
 };
+
+constexpr float kHalfLog2e = -0.72134752044448170368f;   // -1 / (2 ln 2)
+constexpr float kLog2Rsqrt2Pi = -1.32574806473616f;      // log2(1 / sqrt(2 pi))
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 constexpr float kRsqrt2 = 0.70710678118654752440f;      // 1 / sqrt(2)
 constexpr float kRsqrt2Pi = 0.39894228040143267794f;    // 1 / sqrt(2 pi)
@@ -71,7 +94,7 @@ __device__ __forceinline__ float normal_cdf(float x) {
 
 // N(x) from the tail polynomial of A&S 26.2.17 and z = phi(x)
 __device__ __forceinline__ float normal_cdf_poly(float x, float z) {
-  const float t = __fdividef(1.0f, __fmaf_rn(0.2316419f, fabsf(x), 1.0f));
+  const float t = rcp_approx(__fmaf_rn(0.2316419f, fabsf(x), 1.0f));
   float poly = 1.330274429f;
   poly = __fmaf_rn(poly, t, -1.821255978f);
   poly = __fmaf_rn(poly, t, 1.781477937f);
@@ -84,15 +107,17 @@ __device__ __forceinline__ float normal_cdf_poly(float x, float z) {
 template <int CND>
 __device__ __forceinline__ void bs_option(float S, const BsConst& c, float& call, float& put) {
   const float q = __fmul_rn(S, c.inv_k);
-  const float d1 = __fmul_rn(__fadd_rn(CND == 2 ? __logf(q) : logf(q), c.mu), c.inv_sq);
-  const float d2 = __fsub_rn(d1, c.sq);
-  float n1, n2;
+  float d1, n1, n2;
   if constexpr (CND == 2) {
-    const float z1 = __fmul_rn(kRsqrt2Pi, expf(__fmul_rn(-0.5f, __fmul_rn(d1, d1))));
+    d1 = __fmaf_rn(lg2_approx(q), c.ln2_sq, c.mu_sq);
+    const float d2 = __fsub_rn(d1, c.sq);
+    const float z1 = ex2_approx(__fmaf_rn(d1, __fmul_rn(d1, kHalfLog2e), kLog2Rsqrt2Pi));
     const float z2 = __fmul_rn(__fmul_rn(z1, S), c.inv_ke);
     n1 = normal_cdf_poly(d1, z1);
     n2 = normal_cdf_poly(d2, z2);
   } else {
+    d1 = __fmul_rn(__fadd_rn(logf(q), c.mu), c.inv_sq);
+    const float d2 = __fsub_rn(d1, c.sq);
     n1 = normal_cdf<CND>(d1);
     n2 = normal_cdf<CND>(d2);
   }
@@ -154,6 +179,8 @@ struct BlackScholes {
     c.inv_sq = (float)(1.0 / (sig * sqrt(T)));
     c.ke = (float)(K * exp(-r * T));
     c.inv_ke = (float)(1.0 / (K * exp(-r * T)));
+    c.ln2_sq = (float)(log(2.0) / (sig * sqrt(T)));
+    c.mu_sq = (float)((r + 0.5 * sig * sig) * T / (sig * sqrt(T)));
     int64_t n = a.n;
     const float* prices = static_cast<const float*>(a.x);
     float* call = a.out;
