@@ -30,7 +30,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int64_t kItemBytes = 256 * 1024;   // target bytes moved per work item
-constexpr int kCombine = 256;
 
 // vector-op processing modes: (VW, J) with TILE = kThreads * VW * J
 struct VecMode {

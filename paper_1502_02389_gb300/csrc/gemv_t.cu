@@ -86,46 +86,45 @@ __global__ void __launch_bounds__(THREADS)
     }
   }
 
-  if (PASSES == 2) {
+  if constexpr (PASSES == 2) {
     // the combine kernel may start launching; it waits for this grid to end
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 #pragma unroll
     for (int l = 0; l < VW; ++l)
       if (c0 + l < N) partials[(c0 + l) * RB + rb] = acc[l];
-    return;
-  }
+  } else {
+#pragma unroll
+    for (int l = 0; l < VW; ++l)
+      if (c0 + l < N) partials[rb * N + c0 + l] = acc[l];
 
-#pragma unroll
-  for (int l = 0; l < VW; ++l)
-    if (c0 + l < N) partials[rb * N + c0 + l] = acc[l];
-
-  __shared__ bool is_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    is_last = atomicAdd(tickets + cb, 1u) == static_cast<unsigned>(RB - 1);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-#pragma unroll
-  for (int l = 0; l < VW; ++l) {
-    const int64_t j = c0 + l;
-    if (j >= N) continue;
-    float s = 0.f;
-    int64_t q = 0;
-    for (; q + 8 <= RB; q += 8) {        // eight loads in flight, added in order
-      float v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = __ldcg(partials + (q + k) * N + j);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s = __fadd_rn(s, v[k]);
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      is_last = atomicAdd(tickets + cb, 1u) == static_cast<unsigned>(RB - 1);
     }
-    for (; q < RB; ++q) s = __fadd_rn(s, __ldcg(partials + q * N + j));
-    const float z = __fmul_rn(alpha, s);
-    y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+#pragma unroll
+    for (int l = 0; l < VW; ++l) {
+      const int64_t j = c0 + l;
+      if (j >= N) continue;
+      float s = 0.f;
+      int64_t q = 0;
+      for (; q + 8 <= RB; q += 8) {        // eight loads in flight, added in order
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __ldcg(partials + (q + k) * N + j);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s = __fadd_rn(s, v[k]);
+      }
+      for (; q < RB; ++q) s = __fadd_rn(s, __ldcg(partials + q * N + j));
+      const float z = __fmul_rn(alpha, s);
+      y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
+    }
+    if (threadIdx.x == 0) tickets[cb] = 0u;   // ready for the next call
   }
-  if (threadIdx.x == 0) tickets[cb] = 0u;   // ready for the next call
 }
 
 // Second pass: column j's RB partials P[j][0..RB) -> y_j.  Warp w of the
