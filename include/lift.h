@@ -74,7 +74,9 @@ typedef enum {
   LIFT_OP_AXPY = 10,
   LIFT_OP_GEMV_T = 11,
   LIFT_OP_BLACKSCHOLES = 12,
-  LIFT_NUM_OPS = 13
+  LIFT_OP_ASUM_COMP = 13,
+  LIFT_OP_DOT_COMP = 14,
+  LIFT_NUM_OPS = 15
 } lift_op;
 
 /* The cost model covers op ids 0 .. LIFT_MLP_OPS-1; the MLP policy falls
@@ -188,6 +190,29 @@ lift_status lift_gemv_t_v(int variant, int64_t M, int64_t N, float alpha, const 
                           int64_t lda, const float* x, float beta, float* y, void* stream);
 lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_per_block,
                                int64_t* blocks);
+
+/* ------------------------------------------------------------------------
+ * Compensated fp32 asum and dot: the Fig. 5 programs with an error-free
+ * fold.  Every term is added to a per-lane (sum, compensation) pair with
+ * TwoSum; for dot the product's rounding error, fma(x, y, -fl(x y)), is
+ * added to the compensation too (TwoProduct, Ogita, Rump and Oishi 2005).
+ * The pairs are merged with TwoSum across lanes, the warp and the CTA, the
+ * per-CTA values sum + compensation are added in FP64 and rounded once to
+ * fp32.  The result is within about one unit of fp32 roundoff of the exact
+ * value (plus a second-order term), also when the sum cancels.
+ * x, y: n floats (device); result: one float (device); result_f64
+ * (optional): the FP64 value before the rounding.  Arguments, errors and
+ * alignment fallback as for lift_asum / lift_dot; uses the lift_init
+ * workspace (FP64 partial slots and one counter).
+ * ------------------------------------------------------------------------ */
+lift_status lift_asum_comp(const float* x, int64_t n, float* result, double* result_f64,
+                           void* stream);
+lift_status lift_dot_comp(const float* x, const float* y, int64_t n, float* result,
+                          double* result_f64, void* stream);
+lift_status lift_asum_comp_v(int variant, const float* x, int64_t n, float* result,
+                             double* result_f64, void* stream);
+lift_status lift_dot_comp_v(int variant, const float* x, const float* y, int64_t n, float* result,
+                            double* result_f64, void* stream);
 
 /* ------------------------------------------------------------------------
  * BlackScholes (Sec. 7 "Mathematical Finance Application", Fig. 6):

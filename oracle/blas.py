@@ -119,6 +119,29 @@ def axpy(a, x, y, mode="f64"):
     return evaluate(axpy_expr(), (scal(a, x, mode), y), mode)
 
 
+def asum_exact(x) -> float:
+    """sum |x_i|, correctly rounded to FP64 (math.fsum)."""
+    return math.fsum(np.abs(np.asarray(x, np.float64)))
+
+
+def dot_exact(x, y) -> float:
+    """sum x_i y_i, correctly rounded to FP64: the product of two fp32
+    values is exact in FP64 (24 + 24 significant bits), and math.fsum adds
+    the exact products with a single final rounding."""
+    return math.fsum(np.asarray(x, np.float64) * np.asarray(y, np.float64))
+
+
+def compensated_tolerance(value: float, sum_abs_terms: float, m: int) -> float:
+    """Bound for a compensated sum: every term added with TwoSum into one of
+    several (sum, compensation) pairs, at most m terms per pair, pairs merged
+    with TwoSum, the result rounded once to fp32.  The compensated sum of m
+    terms is within u|s| + gamma_m^2 sum|t| of the exact s (Ogita, Rump and
+    Oishi 2005, Sum2; gamma_m ~ m u); the fp32 rounding adds u|s|.  With a
+    factor 2 on the second-order term for the merges:
+    2 u |v| + 2 (m u)^2 sum|t|."""
+    return 2 * U_FP32 * abs(value) + 2 * (m * U_FP32) ** 2 * float(sum_abs_terms)
+
+
 def nrm2_tolerance(n: int, sum_sq: float) -> float:
     """nrm2 = sqrt(S) with S = sum x_i^2 (all terms >= 0, so sum|terms| = S).
     An error e <= 4 u ceil(log2 n) S in S moves the root by

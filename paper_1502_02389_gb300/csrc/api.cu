@@ -101,6 +101,7 @@ void register_gemv_t(std::vector<Variant>& gemv_t);   // gemv_t.cu
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB);
 void register_gemv_split(std::vector<Variant>& gemv);  // gemv_split.cu
 void register_blackscholes(std::vector<Variant>& bs);  // blackscholes.cu
+void register_compensated(std::vector<Variant>& asum, std::vector<Variant>& dot);  // compensated.cu
 void register_reduce_derived(std::vector<Variant>& asum, std::vector<Variant>& dot);  // reduce_derived.cu
 void gemv_split_shape(int k, const Args& a, int64_t* L, int64_t* S);
 lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s);
@@ -120,6 +121,7 @@ static void build_registry() {
   register_axpy(g_ops[LIFT_OP_AXPY]);
   register_gemv_t(g_ops[LIFT_OP_GEMV_T]);
   register_blackscholes(g_ops[LIFT_OP_BLACKSCHOLES]);
+  register_compensated(g_ops[LIFT_OP_ASUM_COMP], g_ops[LIFT_OP_DOT_COMP]);
 }
 
 std::vector<Variant>& registry(int op) {
@@ -187,7 +189,7 @@ struct Mlp {
 };
 
 static int g_policy = LIFT_POLICY_FIXED;
-static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+static int g_override[LIFT_NUM_OPS] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 static std::vector<TableEntry> g_table[LIFT_NUM_OPS];
 static Mlp g_mlp;
 static std::mutex g_policy_mu;
@@ -199,7 +201,7 @@ static const char* kDefaultName[LIFT_NUM_OPS] = {
     "asum_t4096_v4_ldg_p1", "dot_t4096_v4_ldg_p1", "scal_t1024_v4_ldg", "gemv_tma_w8_c1024_s3",
     "asum_bf16_t256_u4",    "dot_bf16_t256_u8",    "asum_fp8_t256_u4",  "dot_fp8_t256_u4",
     "nrm2_t4096_v4_ldg_p1", "sum_t4096_v4_ldg_p1", "axpy_t1024_v4_ldg", "gemv_t_t256_v4_u4_p2",
-    "blackscholes_t128_v4_u4_fast"};
+    "blackscholes_t128_v4_u4_fast", "asum_comp_t256_v4_u4", "dot_comp_t256_v4_u4"};
 
 static int find_variant(int op, const char* name) {
   auto& L = registry(op);
@@ -415,6 +417,44 @@ lift_status lift_asum_v(int variant, const float* x, int64_t n, float* result, d
   a.result = result;
   a.result64 = result_f64;
   return run(LIFT_OP_ASUM, variant, a, stream);
+}
+
+lift_status lift_asum_comp_v(int variant, const float* x, int64_t n, float* result,
+                             double* result_f64, void* stream) {
+  if (bad_n(n) || !result || (n > 0 && !x))
+    return set_error(LIFT_ERR_INVALID_ARG, "asum_comp arguments");
+  if (!aligned(x, 4)) return set_error(LIFT_ERR_INVALID_ARG, "x not 4-byte aligned");
+  Args a;
+  a.x = x;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(LIFT_OP_ASUM_COMP, variant, a, stream);
+}
+
+lift_status lift_dot_comp_v(int variant, const float* x, const float* y, int64_t n, float* result,
+                            double* result_f64, void* stream) {
+  if (bad_n(n) || !result || (n > 0 && (!x || !y)))
+    return set_error(LIFT_ERR_INVALID_ARG, "dot_comp arguments");
+  if (!aligned(x, 4) || !aligned(y, 4))
+    return set_error(LIFT_ERR_INVALID_ARG, "x/y not 4-byte aligned");
+  Args a;
+  a.x = x;
+  a.y = y;
+  a.n = n;
+  a.result = result;
+  a.result64 = result_f64;
+  return run(LIFT_OP_DOT_COMP, variant, a, stream);
+}
+
+lift_status lift_asum_comp(const float* x, int64_t n, float* result, double* result_f64,
+                           void* stream) {
+  return lift_asum_comp_v(-1, x, n, result, result_f64, stream);
+}
+
+lift_status lift_dot_comp(const float* x, const float* y, int64_t n, float* result,
+                          double* result_f64, void* stream) {
+  return lift_dot_comp_v(-1, x, y, n, result, result_f64, stream);
 }
 
 lift_status lift_dot_v(int variant, const float* x, const float* y, int64_t n, float* result,

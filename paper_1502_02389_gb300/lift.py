@@ -20,12 +20,12 @@ LIB_PATH = os.path.join(HERE, "liftblas.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NO_MEMORY, ERR_TIMEOUT, ERR_NOT_INITIALIZED = range(7)
 F32, BF16, FP8_E4M3 = 0, 1, 2
 (OP_ASUM, OP_DOT, OP_SCAL, OP_GEMV, OP_ASUM_BF16, OP_DOT_BF16, OP_ASUM_FP8, OP_DOT_FP8, OP_NRM2,
- OP_SUM, OP_AXPY, OP_GEMV_T, OP_BLACKSCHOLES) = range(13)
-NUM_OPS = 13
+ OP_SUM, OP_AXPY, OP_GEMV_T, OP_BLACKSCHOLES, OP_ASUM_COMP, OP_DOT_COMP) = range(15)
+NUM_OPS = 15
 MLP_OPS = 8     # op ids the cost model covers
 NUM_FEATURES = 12   # lift_features output length
 OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8", "nrm2",
-            "sum", "axpy", "gemv_t", "blackscholes"]
+            "sum", "axpy", "gemv_t", "blackscholes", "asum_comp", "dot_comp"]
 POLICY_FIXED, POLICY_TABLE, POLICY_MLP = 0, 1, 2
 
 
@@ -81,6 +81,10 @@ _SIGS = {
     "lift_asum_noalloc": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_nrm2": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_gemv_t": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
+    "lift_asum_comp": ([_P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_dot_comp": ([_P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_asum_comp_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "lift_dot_comp_v": ([ctypes.c_int, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
     "lift_blackscholes": ([_I64, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            _P, _P, _P], ctypes.c_int),
     "lift_blackscholes_v": ([ctypes.c_int, _I64, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -218,6 +222,26 @@ def lift_scal_v(variant, n, alpha, x, y, stream=None):
 def lift_gemv_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
     _check(lib().lift_gemv_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
                              _stream(stream)), "lift_gemv_v")
+
+
+def lift_asum_comp(x, n, result, result_f64=None, stream=None):
+    _check(lib().lift_asum_comp(_ptr(x), n, _ptr(result), _ptr(result_f64), _stream(stream)),
+           "lift_asum_comp")
+
+
+def lift_dot_comp(x, y, n, result, result_f64=None, stream=None):
+    _check(lib().lift_dot_comp(_ptr(x), _ptr(y), n, _ptr(result), _ptr(result_f64),
+                               _stream(stream)), "lift_dot_comp")
+
+
+def lift_asum_comp_v(variant, x, n, result, result_f64=None, stream=None):
+    _check(lib().lift_asum_comp_v(variant, _ptr(x), n, _ptr(result), _ptr(result_f64),
+                                  _stream(stream)), "lift_asum_comp_v")
+
+
+def lift_dot_comp_v(variant, x, y, n, result, result_f64=None, stream=None):
+    _check(lib().lift_dot_comp_v(variant, _ptr(x), _ptr(y), n, _ptr(result), _ptr(result_f64),
+                                 _stream(stream)), "lift_dot_comp_v")
 
 
 def lift_blackscholes(n, s, strike, rate, volatility, years, call, put, stream=None):

@@ -32,8 +32,10 @@ MIXED = (lift.OP_ASUM_BF16, lift.OP_DOT_BF16, lift.OP_ASUM_FP8, lift.OP_DOT_FP8)
 
 def op_bytes(op: int, n: int, M: int = 0, N: int = 0) -> int:
     """Algorithmic bytes one call moves."""
-    if op in (lift.OP_ASUM, lift.OP_NRM2, lift.OP_SUM):
+    if op in (lift.OP_ASUM, lift.OP_NRM2, lift.OP_SUM, lift.OP_ASUM_COMP):
         return 4 * n
+    if op == lift.OP_DOT_COMP:
+        return 8 * n
     if op in (lift.OP_AXPY, lift.OP_BLACKSCHOLES):
         return 12 * n
     if op == lift.OP_DOT:
@@ -128,6 +130,12 @@ class Buffers:
         if op == lift.OP_AXPY:
             x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
             return lambda: lift.lift_axpy_v(vid, n, 1.5, x, y)
+        if op == lift.OP_ASUM_COMP:
+            x = self._slice("x", "f32", r, n)
+            return lambda: lift.lift_asum_comp_v(vid, x, n, res)
+        if op == lift.OP_DOT_COMP:
+            x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
+            return lambda: lift.lift_dot_comp_v(vid, x, y, n, res)
         if op == lift.OP_DOT:
             x, y = self._slice("x", "f32", r, n), self._slice("y", "f32", r, n)
             return lambda: lift.lift_dot_v(vid, x, y, n, res)
@@ -303,7 +311,8 @@ def write_table(records: List[Dict], path: str) -> None:
 def workload_shapes() -> List[Tuple[int, int, int, int]]:
     """The benchmark configurations: asum 2^20, dot / scal / asum 2^26, the
     two gemv shapes, the mixed ops at 2^28, nrm2 / sum / axpy 2^26, the two
-    gemv-T shapes, BlackScholes at 2^22 (the paper's size) and 2^26."""
+    gemv-T shapes, BlackScholes at 2^22 (the paper's size) and 2^26, the
+    compensated asum / dot at 2^26."""
     s = [(lift.OP_ASUM, 1 << 20, 0, 0), (lift.OP_DOT, 1 << 26, 0, 0), (lift.OP_SCAL, 1 << 26, 0, 0),
          (lift.OP_ASUM, 1 << 26, 0, 0),
          (lift.OP_GEMV, 8192 * 8192, 8192, 8192), (lift.OP_GEMV, 65536 * 1024, 65536, 1024)]
@@ -311,6 +320,7 @@ def workload_shapes() -> List[Tuple[int, int, int, int]]:
     s += [(op, 1 << 26, 0, 0) for op in (lift.OP_NRM2, lift.OP_SUM, lift.OP_AXPY)]
     s += [(lift.OP_GEMV_T, 8192 * 8192, 8192, 8192), (lift.OP_GEMV_T, 65536 * 1024, 65536, 1024)]
     s += [(lift.OP_BLACKSCHOLES, 1 << 22, 0, 0), (lift.OP_BLACKSCHOLES, 1 << 26, 0, 0)]
+    s += [(lift.OP_ASUM_COMP, 1 << 26, 0, 0), (lift.OP_DOT_COMP, 1 << 26, 0, 0)]
     return s
 
 

@@ -196,3 +196,25 @@ def test_gemv_t_brute_force(seed):
                  + Fraction(1, 4) * Fraction(y[j])) for j in range(N)]
     assert out.tolist() == exp
     assert blas.gemv_t(np.zeros((0, N)), np.zeros(0), y, 1.0, 0.5).tolist() == (0.5 * y).tolist()
+
+
+def test_exact_sums_are_correctly_rounded():
+    # a left fold loses the 1 entirely; the exact sums keep it
+    x = np.array([2.0 ** 60, 1.0, -(2.0 ** 60)])
+    assert blas.dot_exact(x, np.ones(3)) == 1.0
+    assert blas.asum_exact(np.array([2.0 ** 52, 0.5, -(2.0 ** 52)])) == 2.0 ** 53   # ties to even
+    # a left fold rounds 1 + 2^-53 back to 1 twice; the exact sum is 1 + 2^-52
+    assert blas.asum_exact(np.array([1.0, -(2.0 ** -53), 2.0 ** -53])) == 1 + 2.0 ** -52
+    assert blas.asum(np.array([1.0, -(2.0 ** -53), 2.0 ** -53])) == 1.0
+    # fp32 products are exact in FP64: (1 + 2^-23)^2 = 1 + 2^-22 + 2^-46
+    a = np.array([np.float32(1 + 2 ** -23)], np.float32)
+    assert blas.dot_exact(a, a) == 1 + 2 ** -22 + 2 ** -46
+    rng = np.random.default_rng(4)
+    p = rng.integers(-(1 << 20), 1 << 20, 5000).astype(float)
+    q = rng.integers(-(1 << 20), 1 << 20, 5000).astype(float)
+    assert blas.dot_exact(p, q) == float(int(np.sum(p.astype(object) * q.astype(object))))
+
+
+def test_compensated_tolerance_formula():
+    u = 2.0 ** -24
+    assert blas.compensated_tolerance(-3.0, 100.0, 10) == 2 * u * 3 + 2 * (10 * u) ** 2 * 100
