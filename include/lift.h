@@ -417,6 +417,16 @@ lift_status lift_mlp_backward(int d_in, int h1, int h2, int V, const float* para
 lift_status lift_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t count,
                           int t, float lr, float beta1, float beta2, float eps, void* stream);
 
+/* Failure-detection probe (the paper has no counterpart).  Launches, on
+ * `stream`, one warp whose first lane waits on an mbarrier that nothing
+ * arrives at, giving up after `polls` polls (1 .. 2^22, the limit every
+ * staged kernel uses) and recording LIFT_ERR_TIMEOUT in the device status
+ * word -- the path a bulk-copy pipeline takes when its copies stall.  Faults
+ * nothing and leaves the context usable; read (and clear) the outcome with
+ * lift_read_status(1).  Errors: LIFT_ERR_INVALID_ARG for polls out of range,
+ * LIFT_ERR_NOT_INITIALIZED without lift_init. */
+lift_status lift_wait_probe(uint32_t polls, void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free asum.  The paper has no counterpart: this entry point
  * exists for callers that must not have the library allocate device memory

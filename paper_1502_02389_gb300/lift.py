@@ -81,6 +81,7 @@ _SIGS = {
     "lift_asum_noalloc": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_nrm2": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_gemv_t": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
+    "lift_wait_probe": ([ctypes.c_uint32, _P], ctypes.c_int),
     "lift_asum_comp": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "lift_dot_comp": ([_P, _P, _I64, _P, _P, _P], ctypes.c_int),
     "lift_asum_comp_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
@@ -222,6 +223,10 @@ def lift_scal_v(variant, n, alpha, x, y, stream=None):
 def lift_gemv_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
     _check(lib().lift_gemv_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
                              _stream(stream)), "lift_gemv_v")
+
+
+def lift_wait_probe(polls, stream=None):
+    _check(lib().lift_wait_probe(polls, _stream(stream)), "lift_wait_probe")
 
 
 def lift_asum_comp(x, n, result, result_f64=None, stream=None):
