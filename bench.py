@@ -55,7 +55,7 @@ WORKLOADS = {
 }
 
 
-E2E_CHUNKS = 16     # slices of the end-to-end pipeline
+E2E_CHUNKS = 8      # slices of the end-to-end pipeline (16 measured slower: 310 vs 348 GB/s)
 
 
 def peaks():
