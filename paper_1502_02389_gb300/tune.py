@@ -218,7 +218,7 @@ def load_db(path: str) -> List[Dict]:
     return out
 
 
-def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], reps: int = 10,
+def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], reps: int = 20,
           warmup: int = 2, variants: Optional[Dict[int, List[int]]] = None,
           verbose: bool = False) -> List[Dict]:
     """Time every variant of each (op, n, M, N); returns the new records."""
@@ -354,7 +354,7 @@ def main():
     ap.add_argument("--preset", default="workloads", choices=["workloads", "train", "heldout"])
     ap.add_argument("--count", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=11)
-    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--table", default=None)
     ap.add_argument("--csv", default=None)
     ap.add_argument("--ops", type=int, nargs="+", default=None,
