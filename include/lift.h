@@ -79,9 +79,10 @@ typedef enum {
   LIFT_NUM_OPS = 15
 } lift_op;
 
-/* The cost model covers op ids 0 .. LIFT_MLP_OPS-1; the MLP policy falls
- * back to the FIXED choice for the others. */
-#define LIFT_MLP_OPS 8
+/* The cost model can cover op ids 0 .. LIFT_MLP_OPS-1 (a weights file says
+ * how many it covers); the MLP policy falls back to the FIXED choice for the
+ * others. */
+#define LIFT_MLP_OPS 15
 
 /* ------------------------------------------------------------------------
  * Library state
@@ -324,11 +325,13 @@ lift_status lift_set_variant(int op, int variant);
 lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant);
 
 /* The LIFT_NUM_FEATURES cost-model features of a call, written to
- * out[0..11]: one-hot op family (asum, dot, scal, gemv), log2(n+1)/32,
- * log2(M+1)/16, log2(N+1)/16, one-hot element type (fp32, bf16, fp8), and,
- * gemv only, whether a dense row holds whole 16-byte and whole 32-byte
- * vectors (N % 4 == 0, N % 8 == 0; 0 for the other ops).  For gemv the
- * size feature uses n = M*N.  A weights file with d_in < 12 reads the first
+ * out[0..11]: one-hot op family (asum-like one-input reductions: asum,
+ * nrm2, sum, compensated asum; dot-like: dot, compensated dot; maps: scal,
+ * axpy, BlackScholes; matrices: gemv, gemv-T), log2(n+1)/32, log2(M+1)/16,
+ * log2(N+1)/16, one-hot element type (fp32, bf16, fp8), and, gemv and
+ * gemv-T only, whether a dense row holds whole 16-byte and whole 32-byte
+ * vectors (N % 4 == 0, N % 8 == 0; 0 for the other ops).  For gemv and
+ * gemv-T the size feature uses n = M*N.  A weights file with d_in < 12 reads the first
  * d_in.  Host-only; needs no device.  Defined for op ids below LIFT_MLP_OPS
  * (LIFT_ERR_INVALID_ARG otherwise). */
 #define LIFT_NUM_FEATURES 12

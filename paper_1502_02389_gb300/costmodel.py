@@ -173,8 +173,8 @@ def save(path: str, params: np.ndarray, V: int, off: Optional[List[int]] = None)
     if off is None:
         off, _ = offsets()
     with open(path, "w") as f:
-        f.write(f"lift-mlp 1 {D_IN} {H1} {H2} {V}\n")
-        f.write("offsets " + " ".join(str(o) for o in off) + "\n")
+        f.write(f"lift-mlp 2 {D_IN} {H1} {H2} {V}\n")
+        f.write(f"offsets {len(off)} " + " ".join(str(o) for o in off) + "\n")
         f.write(" ".join(f"{x:.9g}" for x in params.tolist()) + "\n")
 
 

@@ -184,6 +184,7 @@ struct TableEntry {
 
 struct Mlp {
   int d_in = 0, h1 = 0, h2 = 0, V = 0;
+  int ops = 0;                       // op ids 0 .. ops-1 have an output slice
   int offsets[LIFT_MLP_OPS] = {0};
   std::vector<float> W1, b1, W2, b2, W3, b3;
 };
@@ -222,16 +223,17 @@ extern "C" {
 // (fp32, bf16, fp8).  For gemv n = M*N.
 lift_status lift_features(int op, int64_t n, int64_t M, int64_t N, float* out) {
   if (op < 0 || op >= LIFT_MLP_OPS || !out) return LIFT_ERR_INVALID_ARG;
-  static const int fam[LIFT_MLP_OPS] = {0, 1, 2, 3, 0, 1, 0, 1};
-  static const int dt[LIFT_MLP_OPS] = {0, 0, 0, 0, 1, 1, 2, 2};
+  static const int fam[LIFT_MLP_OPS] = {0, 1, 2, 3, 0, 1, 0, 1, 0, 0, 2, 3, 2, 0, 1};
+  static const int dt[LIFT_MLP_OPS] = {0, 0, 0, 0, 1, 1, 2, 2, 0, 0, 0, 0, 0, 0, 0};
   for (int i = 0; i < LIFT_NUM_FEATURES; ++i) out[i] = 0.f;
   out[fam[op]] = 1.f;
-  if (op == LIFT_OP_GEMV) n = M * N;
+  const bool matrix = op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T;
+  if (matrix) n = M * N;
   out[4] = (float)(log2((double)n + 1.0) / 32.0);
   out[5] = (float)(log2((double)M + 1.0) / 16.0);
   out[6] = (float)(log2((double)N + 1.0) / 16.0);
   out[7 + dt[op]] = 1.f;
-  if (op == LIFT_OP_GEMV) {     // whole 16- and 32-byte vectors per dense row
+  if (matrix) {                 // whole 16- and 32-byte vectors per dense row
     out[10] = N % 4 == 0 ? 1.f : 0.f;
     out[11] = N % 8 == 0 ? 1.f : 0.f;
   }
@@ -276,10 +278,10 @@ static int mlp_pick(int op, const Args& a) {
   }
   // variants the weights know: the file's slice of this op (a registry that
   // grew after training keeps its newer variants out of the pick)
-  const int file_cnt = (op + 1 < LIFT_MLP_OPS ? m.offsets[op + 1] : m.V) - m.offsets[op];
+  const int file_cnt = (op + 1 < m.ops ? m.offsets[op + 1] : m.V) - m.offsets[op];
   const auto& L = registry(op);
   const int cnt = std::min((int)L.size(), file_cnt);
-  int best = 0;
+  int best = -1;                      // none: the caller falls back to the FIXED choice
   float best_t = INFINITY;
   for (int v = 0; v < cnt; ++v) {
     const int o = m.offsets[op] + v;
@@ -321,7 +323,7 @@ static int pick_variant(int op, const Args& a) {
   std::lock_guard<std::mutex> lk(g_policy_mu);
   if (g_override[op] >= 0) return g_override[op];
   int v = -1;
-  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < LIFT_MLP_OPS) v = mlp_pick(op, a);
+  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < g_mlp.ops) v = mlp_pick(op, a);
   if (g_policy == LIFT_POLICY_TABLE) v = table_pick(op, a);
   if (v < 0) v = find_variant(op, kDefaultName[op]);
   return v;
@@ -749,9 +751,10 @@ lift_status lift_set_variant(int op, int variant) {
 
 // Table file: one line per entry "op log2(n+1) log2(M+1) log2(N+1) variant"
 // (gemv: n = M*N); '#' starts a comment.
-// MLP file: "lift-mlp 1 d_in h1 h2 V", then "offsets" and LIFT_NUM_OPS
-// integers, then W1 b1 W2 b2 W3 b3 as whitespace-separated floats
-// (W_k row-major [d_(k-1)][d_k]).
+// MLP file: "lift-mlp 2 d_in h1 h2 V", then "offsets K" and K integers (the
+// first output of op ids 0 .. K-1; version 1 files have K = 8 without the
+// count), then W1 b1 W2 b2 W3 b3 as whitespace-separated floats (W_k
+// row-major [d_(k-1)][d_k]).
 lift_status lift_set_policy(int policy, const char* path) {
   if (policy == LIFT_POLICY_FIXED) {
     std::lock_guard<std::mutex> lk(g_policy_mu);
@@ -788,7 +791,12 @@ lift_status lift_set_policy(int policy, const char* path) {
         m.d_in > LIFT_NUM_FEATURES)
       return set_error(LIFT_ERR_INVALID_ARG, "bad MLP header");
     if (!(f >> off) || off != "offsets") return set_error(LIFT_ERR_INVALID_ARG, "bad MLP offsets");
-    for (int i = 0; i < LIFT_MLP_OPS; ++i) f >> m.offsets[i];
+    m.ops = 8;
+    if (ver >= 2 && !(f >> m.ops)) return set_error(LIFT_ERR_INVALID_ARG, "bad MLP offsets");
+    if (m.ops < 1 || m.ops > LIFT_MLP_OPS) return set_error(LIFT_ERR_INVALID_ARG, "bad MLP op count");
+    for (int i = 0; i < m.ops; ++i)
+      if (!(f >> m.offsets[i]) || m.offsets[i] < 0 || m.offsets[i] > m.V)
+        return set_error(LIFT_ERR_INVALID_ARG, "bad MLP offsets");
     auto rd = [&](std::vector<float>& w, size_t cnt) {
       w.resize(cnt);
       for (size_t i = 0; i < cnt; ++i)

@@ -22,7 +22,7 @@ F32, BF16, FP8_E4M3 = 0, 1, 2
 (OP_ASUM, OP_DOT, OP_SCAL, OP_GEMV, OP_ASUM_BF16, OP_DOT_BF16, OP_ASUM_FP8, OP_DOT_FP8, OP_NRM2,
  OP_SUM, OP_AXPY, OP_GEMV_T, OP_BLACKSCHOLES, OP_ASUM_COMP, OP_DOT_COMP) = range(15)
 NUM_OPS = 15
-MLP_OPS = 8     # op ids the cost model covers
+MLP_OPS = 15    # op ids a cost model can cover (all of them)
 NUM_FEATURES = 12   # lift_features output length
 OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8", "nrm2",
             "sum", "axpy", "gemv_t", "blackscholes", "asum_comp", "dot_comp"]

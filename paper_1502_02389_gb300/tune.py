@@ -324,6 +324,11 @@ def workload_shapes() -> List[Tuple[int, int, int, int]]:
     return s
 
 
+# op ids of the first training distribution (asum, dot, scal, gemv and the
+# four mixed-precision ops); the others are drawn by passing ``ops``
+DEFAULT_SHAPE_OPS = tuple(range(8))
+
+
 def random_shapes(count: int, seed: int, ops: Optional[List[int]] = None,
                   lo: int = 8, hi: int = 28,
                   gemv_range: Tuple[float, float] = (6, 14),
@@ -332,11 +337,11 @@ def random_shapes(count: int, seed: int, ops: Optional[List[int]] = None,
     round(2^U(lo, hi)); gemv M, N = round(2^U(gemv_range)) (N rounded up to
     a multiple of ``align_n``) with 2^8 <= M*N <= 2^28."""
     rng = np.random.default_rng(seed)
-    ops = ops or list(range(lift.MLP_OPS))
+    ops = ops or list(DEFAULT_SHAPE_OPS)
     out = []
     while len(out) < count:
         op = int(rng.choice(ops))
-        if op == lift.OP_GEMV:
+        if op in (lift.OP_GEMV, lift.OP_GEMV_T):
             M = int(round(2 ** rng.uniform(*gemv_range)))
             N = int(round(2 ** rng.uniform(*gemv_range)))
             N = -(-N // align_n) * align_n

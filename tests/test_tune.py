@@ -58,7 +58,9 @@ def test_op_bytes_and_shapes():
     assert s == tune.random_shapes(300, seed=1)
     assert all(2 ** 8 - 1 <= n <= 2 ** 28 + 1 for op, n, M, N in s if op != lift.OP_GEMV)
     assert all(M * N == n and M * N <= 2 ** 28 for op, n, M, N in s if op == lift.OP_GEMV)
-    assert {op for op, *_ in s} == set(range(lift.MLP_OPS))
+    assert {op for op, *_ in s} == set(tune.DEFAULT_SHAPE_OPS)
+    t = tune.random_shapes(200, seed=2, ops=[lift.OP_GEMV_T, lift.OP_NRM2])
+    assert all(M * N == n for op, n, M, N in t if op == lift.OP_GEMV_T)
 
 
 @pytest.mark.gpu
