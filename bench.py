@@ -239,6 +239,7 @@ def run_ours(args, rank, world, dist):
     launches_per_step = 0
     kernels = []   # (tag, bytes per launch, start events, end events)
     flushed = False  # True: an L2 flush runs between the timed spans of each step
+    collect = None   # after the timed steps: the GPU results the oracle leg checks
 
     for name in args.variant or []:          # pin variants by name (profiling)
         for op in range(lift.NUM_OPS):
@@ -348,6 +349,7 @@ def run_ours(args, rank, world, dist):
         host = dict(xp=torch.from_numpy(xh).pin_memory(), yp=torch.from_numpy(yh).pin_memory(),
                     zp=torch.empty(n, dtype=torch.float32).pin_memory(),
                     rp=torch.empty(C, dtype=torch.float32).pin_memory())
+        collect = lambda: {"dot": float(r.item()), "scal": z.cpu().numpy()}  # noqa: E731
         h2d, d2h = 8 * n, 4 * n + 4 * C
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pd["name"], ps["name"]],
                   "submitted_as": ("one batched launch of the two calls (lift_batch_run)"
@@ -359,7 +361,6 @@ def run_ours(args, rank, world, dist):
         xv, yv = synth.mixed_values(n)
         bx, by = synth.encode_bf16(xv), synth.encode_bf16(yv)
         (qx, sx), (qy, sy) = synth.encode_fp8_blocks(xv), synth.encode_fp8_blocks(yv)
-        del xv, yv
         t = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
         bxd, byd, qxd, qyd, sxd, syd = t(bx), t(by), t(qx), t(qy), t(sx), t(sy)
         r = torch.zeros(4, device=dev)
@@ -390,6 +391,9 @@ def run_ours(args, rank, world, dist):
                     kernels[i][2].append(a); kernels[i][3].append(b)
 
         e2e_step, host, h2d, d2h = None, {}, 0, 0
+        collect = lambda: {"gpu": dict(zip(("asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8"),  # noqa: E731
+                                           r.cpu().numpy().tolist())),
+                           "inputs": (xv, yv, bx, by, qx, sx, qy, sy)}
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [c[4] for c in calls],
                   "l2": "no flush: every input is at least 256 MiB"}
     elif wl == "asum_large":
@@ -414,6 +418,7 @@ def run_ours(args, rank, world, dist):
                 kas[2].append(ev[0]); kas[3].append(ev[1])
 
         e2e_step, host, h2d, d2h = None, {}, 0, 0
+        collect = lambda: {"asum": float(r.item())}  # noqa: E731
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
                   "l2": "no flush: x is 256 MiB, larger than the 129 MB L2"}
     elif wl == "asum":
@@ -445,6 +450,7 @@ def run_ours(args, rank, world, dist):
             rp.copy_(r, non_blocking=True)
 
         host = dict(xp=torch.from_numpy(xh).pin_memory(), rp=torch.empty(1).pin_memory())
+        collect = lambda: {"asum": float(r.item())}  # noqa: E731
         h2d, d2h = 4 * n, 4
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
                   "l2": "flushed before every step (a 512 MiB read between the timed spans)"}
@@ -495,6 +501,8 @@ def run_ours(args, rank, world, dist):
                     p_h[sl].copy_(put[sl], non_blocking=True)
             s.wait_stream(s_out)
 
+        collect = lambda: {"call": call[:1 << 22].cpu().numpy(),  # noqa: E731
+                           "put": put[:1 << 22].cpu().numpy()}
         host = dict(sp_h=torch.from_numpy(sh).pin_memory(), c_h=torch.empty(n).pin_memory(),
                     p_h=torch.empty(n).pin_memory())
         h2d, d2h = 4 * n, 8 * n
@@ -606,6 +614,13 @@ def run_ours(args, rank, world, dist):
             call(vg, M, N, float(a), A, N, xv, float(b), yv)
             outp.copy_(yv, non_blocking=True)
 
+        def collect():
+            # one call on the initial y (the timed steps update y in place)
+            y1 = y0.clone()
+            call(vg, M, N, float(a), A, N, xv, float(b), y1)
+            idx = np.sort(np.random.default_rng(5).choice(ny, 64, replace=False))
+            return {"index": idx, "y": y1.cpu().numpy()[idx]}
+
         host = dict(Ap=torch.from_numpy(Ah).pin_memory(), xp=torch.from_numpy(xh).pin_memory(),
                     yp=torch.from_numpy(yh).pin_memory(), outp=torch.empty(ny).pin_memory())
         h2d, d2h = 4 * M * N + 4 * nx + 4 * ny, 4 * ny
@@ -701,7 +716,10 @@ def run_ours(args, rank, world, dist):
         for h in handles.values():
             lift.lift_batch_destroy(h)
     assert lift.lift_read_status() == 0
+    results = collect() if (collect is not None and rank == 0) else None
+    torch.cuda.synchronize()
     return dict(value=value, ms_step=ms_step, roofline=roof, per_kernel=per_kernel, clocks=clk,
+                results=results,
                 e2e=e2e, config=config, launches=launches_per_step * args.steps, peak=peak)
 
 
@@ -796,6 +814,85 @@ def oracle_sample(workload: str, budget_s: float):
     return bytes_one * reps / el / 1e9, f"{what}, {reps} repetition(s) in {el:.1f} s", el / reps
 
 
+def oracle_accuracy(workload: str, results):
+    """The GPU results of the run against the oracle (the CPU leg): per result
+    its absolute error and the parity bound (ratio <= 1: within the bound);
+    scal is checked bit for bit.  None when the workload has no check here
+    (the batch is checked op by op in the tests)."""
+    import numpy as np
+
+    from oracle import blas
+    from paper_1502_02389_gb300 import synth
+
+    if not results:
+        return None
+
+    def entry(got, ref, tol):
+        err = abs(float(got) - float(ref))
+        return {"abs_err": err, "tol": float(tol), "ratio": err / tol if tol > 0 else float(err > 0)}
+
+    out = {}
+    if workload == "dot_scal":
+        n = WORKLOADS[workload]["n"]
+        x, y, alpha = synth.dot_scal(n)
+        out["dot"] = entry(results["dot"], blas.dot(x, y), blas.tolerance(n, blas.dot_terms(x, y)))
+        want = (np.float64(alpha) * x.astype(np.float64)).astype(np.float32)
+        out["scal"] = {"bit_exact": bool(np.array_equal(results["scal"], want)), "elements": n}
+    elif workload in ("asum", "asum_large"):
+        n = WORKLOADS[workload]["n"]
+        x = synth.asum_small(n) if workload == "asum" else synth.dot_scal(n)[0]
+        out["asum"] = entry(results["asum"], blas.asum(x), blas.tolerance(n, blas.asum_terms(x)))
+    elif workload == "mixed":
+        from oracle import mixed
+        n = WORKLOADS[workload]["n"]
+        xv, yv, bx, by, qx, sx, qy, sy = results["inputs"]     # the draws and their encodings
+        exact = {"asum": float(np.sum(np.abs(xv))), "dot": float(np.dot(xv, yv))}
+        for dt, (ex, ey) in (("bf16", (mixed.stored_values("bf16", bx), mixed.stored_values("bf16", by))),
+                             ("fp8", (mixed.stored_values("fp8", qx, sx),
+                                      mixed.stored_values("fp8", qy, sy)))):
+            for op in ("asum", "dot"):
+                if op == "asum":
+                    ref, terms = blas.asum(ex), float(np.sum(np.abs(ex)))
+                else:
+                    ref, terms = blas.dot(ex, ey), float(np.sum(np.abs(ex * ey)))
+                e = entry(results["gpu"][f"{op}_{dt}"], ref, blas.tolerance(n, terms))
+                e["quantisation_err"] = abs(ref - exact[op])      # stored values vs FP64 draws
+                out[f"{op}_{dt}"] = e
+            del ex, ey
+    elif workload == "blackscholes":
+        from oracle import finance
+        m = 1 << 22
+        s = synth.stock_prices(WORKLOADS[workload]["n"])[:m]
+        prm = (synth.BS_STRIKE, synth.BS_RATE, synth.BS_VOL, synth.BS_YEARS)
+        c, p = finance.black_scholes(s, *prm)
+        tol = finance.tolerance(s, prm[0], prm[1], prm[3])
+        for name, got, ref in (("call", results["call"], c), ("put", results["put"], p)):
+            ratio = np.abs(got.astype(np.float64) - ref) / tol
+            out[name] = {"max_abs_err": float(np.max(np.abs(got - ref))), "max_ratio": float(np.max(ratio)),
+                         "options": m}
+    elif workload in ("gemv_square", "gemv_tall", "gemv_t_square", "gemv_t_tall"):
+        M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
+        idx = results["index"]
+        if WORKLOADS[workload].get("trans", False):
+            A, x, y, a, b = synth.gemv_t(M, N)
+            As = A[:, idx].astype(np.float64)
+            ref = blas.gemv_t(As, x.astype(np.float64), y[idx].astype(np.float64), float(a), float(b))
+            terms = abs(float(a)) * (np.abs(As).T @ np.abs(x.astype(np.float64))) + \
+                np.abs(float(b) * y[idx].astype(np.float64))
+            n_red = M
+        else:
+            A, x, y, a, b = synth.gemv(M, N)
+            ref = blas.gemv(A[idx].astype(np.float64), x.astype(np.float64), y[idx].astype(np.float64),
+                            float(a), float(b))
+            terms = blas.gemv_row_terms(A[idx], x, y[idx], float(a), float(b))
+            n_red = N
+        ratio = np.abs(results["y"].astype(np.float64) - ref) / (blas.tolerance(n_red, 1.0) * terms)
+        out["y"] = {"max_ratio": float(np.max(ratio)), "sampled_outputs": int(idx.size)}
+    else:
+        return None
+    return out
+
+
 def run_reference(args):
     val, sample, sec = oracle_sample(args.workload, budget_s=max(3.0, 20.0 / max(1, args.steps)))
     out = {"metric": METRIC, "value": round(val, 4), "unit": "GB/s", "n_gpus": args.gpus,
@@ -849,10 +946,12 @@ def main():
     res = run_ours(args, rank, world, dist)
     if rank == 0:
         cpu = None
+        accuracy = None
         if world == 1 and not args.no_cpu_baseline:
             val, sample, _ = oracle_sample(args.workload, budget_s=10.0)
             cpu = {"value": round(val, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                    "sample": sample}
+            accuracy = oracle_accuracy(args.workload, res["results"])
         out = {"metric": METRIC, "value": round(res["value"], 2), "unit": "GB/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": round(res["ms_step"], 5), "higher_is_better": True,
@@ -863,7 +962,7 @@ def main():
                "kernels": {k: {"ms": round(v["ms"], 5), "gbs": round(v["gbs"], 1)}
                            for k, v in res["per_kernel"].items()},
                "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
-               "gpu_launches": res["launches"]}
+               "gpu_launches": res["launches"], "accuracy_vs_oracle": accuracy}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
