@@ -67,12 +67,13 @@ def runs_as_itself(op: int, variant: int, N: int) -> bool:
     return not (op == lift.OP_GEMV and d["stages"] > 0 and (N == 0 or N % 4 != 0))
 
 
-def dataset(records: List[Dict]):
-    """Features X [B, 10], targets T [B, V] = log(t_v / t_best), mask M
-    (the output slices follow ``offsets(records)``).  A timing of a variant
-    that ran its fallback on that shape is masked out: the picks never
-    choose such a variant there."""
-    off, V = offsets(records)
+def dataset(records: List[Dict], off: Optional[List[int]] = None, V: Optional[int] = None):
+    """Features X [B, D_IN], targets T [B, V] = log(t_v / t_best), mask M
+    (the output slices follow ``offsets(records)`` unless given).  A timing
+    of a variant that ran its fallback on that shape is masked out: the
+    picks never choose such a variant there."""
+    if off is None:
+        off, V = offsets(records)
     g = group(records)
     keys = sorted(g)
     X = np.zeros((len(keys), D_IN), np.float32)
@@ -245,18 +246,38 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workloads", default=None,
+                    help="timings of the benchmark shapes, added to the training set with weight")
+    ap.add_argument("--workload-weight", type=int, default=20,
+                    help="rows each benchmark shape counts as in the loss")
     a = ap.parse_args()
     lift.lift_init()
     tr = [r for f in a.train for r in tune.load_csv(f)]
     ho = [r for f in a.heldout for r in tune.load_csv(f)]
-    _, X, T, M = dataset(tr)
+    wl = tune.load_csv(a.workloads) if a.workloads else []
+    off, V = offsets(tr + wl)
+    _, X, T, M = dataset(tr, off, V)
+    if wl:      # the shapes the library is benchmarked on weigh more in the loss
+        _, Xw, Tw, Mw = dataset(wl, off, V)
+        w = a.workload_weight
+        X, T, M = (np.concatenate([A, np.repeat(B, w, axis=0)]) for A, B in ((X, Xw), (T, Tw), (M, Mw)))
     trainer = Trainer(X, T, M, seed=a.seed)
     hist = trainer.train(a.steps, a.lr, log_every=max(1, a.steps // 10))
-    save(a.out, trainer.params(), T.shape[1], offsets(tr)[0])
-    res = evaluate_policies(tr, ho, a.out, a.out + ".table")
-    res.update({"loss": hist, "train_timings": len(tr), "heldout_timings": len(ho),
-                "train_shapes": int(X.shape[0])})
+    save(a.out, trainer.params(), V, off)
+    res = evaluate_policies(tr + wl, ho, a.out, a.out + ".table")
+    if wl:
+        res["workloads"] = summary(regrets(wl, lambda op, n, M, N: _mlp_pick(a.out, op, n, M, N)))
+    res.update({"loss": hist, "train_timings": len(tr), "workload_timings": len(wl),
+                "heldout_timings": len(ho), "train_rows": int(X.shape[0])})
     print(json.dumps(res))
+
+
+def _mlp_pick(weights: str, op, n, M, N) -> int:
+    lift.lift_set_policy(lift.POLICY_MLP, weights)
+    try:
+        return lift.lift_pick(op, n, M, N)
+    finally:
+        lift.lift_set_policy(lift.POLICY_FIXED)
 
 
 if __name__ == "__main__":
