@@ -93,3 +93,17 @@ def test_committed_cost_model_beats_the_method_without_it(L, tmp_path):
     assert res["mlp"]["geomean"] <= 1.10
     assert res["mlp"]["geomean"] < res["best_fixed"]["geomean"]
     assert res["mlp"]["geomean"] < res["table"]["geomean"]
+
+
+def test_committed_cost_model_on_the_benchmark_shapes(L):
+    """On the benchmark configurations (every op's workload shapes, timed with
+    every variant) the learned pick is within 2 % of the exhaustive best."""
+    import os
+    from paper_1502_02389_gb300 import costmodel as cm
+    wl = tune.load_csv(os.path.join(cm.DATA, "timings_gb300_workloads.csv"))
+    L.lift_set_policy(L.POLICY_MLP, cm.WEIGHTS)
+    try:
+        r = cm.regrets(wl, lambda op, n, M, N: L.lift_pick(op, n, M, N))
+    finally:
+        L.lift_set_policy(L.POLICY_FIXED)
+    assert len(r) >= 19 and r.max() <= 1.02
