@@ -193,6 +193,28 @@ lift_status lift_gemv_t_blocks(int variant, int64_t M, int64_t N, int64_t* rows_
                                int64_t* blocks);
 
 /* ------------------------------------------------------------------------
+ * Sharded reductions (the paper has no counterpart; one of the library's
+ * uses over several GPUs).  A rank reduces its shard of the vector(s) to
+ * one FP64 value -- the FP64 sum of its CTAs' fp32 partials, the value
+ * lift_asum / lift_dot round to fp32 -- and the ranks exchange those 8-byte
+ * partials (an all-gather: the one data exchange a sharded asum or dot
+ * needs).  lift_combine_partials adds the gathered partials in index (rank)
+ * order in FP64 and rounds once to fp32, so every rank gets the same result
+ * whatever the order the partials arrived in.
+ * x, y: the shard (device, n floats); partial: one double (device),
+ * written.  partials: `count` doubles (host); result: one float (host);
+ * result_f64 (optional, host): the FP64 sum.  The shard calls use the
+ * policy's variant and the lift_init workspace; lift_combine_partials is
+ * host-only and needs no device.  Errors: LIFT_ERR_INVALID_ARG for bad
+ * sizes or NULL pointers.
+ * ------------------------------------------------------------------------ */
+lift_status lift_asum_partial(const float* x, int64_t n, double* partial, void* stream);
+lift_status lift_dot_partial(const float* x, const float* y, int64_t n, double* partial,
+                             void* stream);
+lift_status lift_combine_partials(const double* partials, int64_t count, float* result,
+                                  double* result_f64);
+
+/* ------------------------------------------------------------------------
  * Compensated fp32 asum and dot: the Fig. 5 programs with an error-free
  * fold.  Every term is added to a per-lane (sum, compensation) pair with
  * TwoSum; for dot the product's rounding error, fma(x, y, -fl(x y)), is

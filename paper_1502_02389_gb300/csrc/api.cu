@@ -421,6 +421,39 @@ lift_status lift_asum_v(int variant, const float* x, int64_t n, float* result, d
   return run(LIFT_OP_ASUM, variant, a, stream);
 }
 
+// The fp32 result of a shard call goes to the last fp32 workspace slot (no
+// kernel uses it: grids and partial counts stay below the capacity).
+static float* shard_discard() {
+  DeviceState* st = current_state();
+  return st ? st->ws.partials + (st->ws.capacity - 1) : nullptr;
+}
+
+lift_status lift_asum_partial(const float* x, int64_t n, double* partial, void* stream) {
+  if (!partial) return set_error(LIFT_ERR_INVALID_ARG, "asum_partial: partial is NULL");
+  float* r = shard_discard();
+  if (!r) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  return lift_asum_v(-1, x, n, r, partial, stream);
+}
+
+lift_status lift_dot_partial(const float* x, const float* y, int64_t n, double* partial,
+                             void* stream) {
+  if (!partial) return set_error(LIFT_ERR_INVALID_ARG, "dot_partial: partial is NULL");
+  float* r = shard_discard();
+  if (!r) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  return lift_dot_v(-1, x, y, n, r, partial, stream);
+}
+
+lift_status lift_combine_partials(const double* partials, int64_t count, float* result,
+                                  double* result_f64) {
+  if (count < 0 || (count > 0 && !partials) || !result)
+    return set_error(LIFT_ERR_INVALID_ARG, "combine_partials arguments");
+  double s = 0.0;
+  for (int64_t i = 0; i < count; ++i) s += partials[i];
+  *result = static_cast<float>(s);
+  if (result_f64) *result_f64 = s;
+  return LIFT_OK;
+}
+
 lift_status lift_asum_comp_v(int variant, const float* x, int64_t n, float* result,
                              double* result_f64, void* stream) {
   if (bad_n(n) || !result || (n > 0 && !x))

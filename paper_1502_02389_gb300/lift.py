@@ -82,6 +82,9 @@ _SIGS = {
     "lift_nrm2": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_gemv_t": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
     "lift_wait_probe": ([ctypes.c_uint32, _P], ctypes.c_int),
+    "lift_asum_partial": ([_P, _I64, _P, _P], ctypes.c_int),
+    "lift_dot_partial": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "lift_combine_partials": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_asum_comp": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "lift_dot_comp": ([_P, _P, _I64, _P, _P, _P], ctypes.c_int),
     "lift_asum_comp_v": ([ctypes.c_int, _P, _I64, _P, _P, _P], ctypes.c_int),
@@ -223,6 +226,25 @@ def lift_scal_v(variant, n, alpha, x, y, stream=None):
 def lift_gemv_v(variant, M, N, alpha, A, lda, x, beta, y, stream=None):
     _check(lib().lift_gemv_v(variant, M, N, alpha, _ptr(A), lda, _ptr(x), beta, _ptr(y),
                              _stream(stream)), "lift_gemv_v")
+
+
+def lift_asum_partial(x, n, partial, stream=None):
+    _check(lib().lift_asum_partial(_ptr(x), n, _ptr(partial), _stream(stream)), "lift_asum_partial")
+
+
+def lift_dot_partial(x, y, n, partial, stream=None):
+    _check(lib().lift_dot_partial(_ptr(x), _ptr(y), n, _ptr(partial), _stream(stream)),
+           "lift_dot_partial")
+
+
+def lift_combine_partials(partials) -> tuple:
+    """Host combine of gathered FP64 partials (a sequence of floats):
+    (fp32 result, FP64 sum)."""
+    arr = (ctypes.c_double * len(partials))(*[float(p) for p in partials])
+    r, r64 = ctypes.c_float(), ctypes.c_double()
+    _check(lib().lift_combine_partials(arr, len(partials), ctypes.byref(r), ctypes.byref(r64)),
+           "lift_combine_partials")
+    return r.value, r64.value
 
 
 def lift_wait_probe(polls, stream=None):
