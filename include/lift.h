@@ -282,7 +282,10 @@ lift_status lift_gemv_v(int variant, int64_t M, int64_t N, float alpha, const fl
  *  stride   1: reorder-stride (thread t reads vector t + threads*j);
  *           0: contiguous chunk per thread
  *  tree     in-CTA iterate depth: 0 warp shuffles only, 1 + shared memory,
- *           2 + cluster distributed shared memory
+ *           2 + cluster distributed shared memory; gemv: 3 = stages filled
+ *           by tensor copies (needs N % 256 == 0); BlackScholes: the normal
+ *           distribution (0 erfcf, 1 polynomial, 2 polynomial on
+ *           approximate instructions)
  *  cluster  CTAs per cluster (1 = none)
  *  passes   1: last-CTA combine in the same launch; 2: second kernel
  *  stages   0: direct vector loads; k >= 2: k-deep TMA bulk-copy ring

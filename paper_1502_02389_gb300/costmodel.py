@@ -64,6 +64,8 @@ def runs_as_itself(op: int, variant: int, N: int) -> bool:
     d = lift.lift_variant_describe(op, variant)
     if (4 * N) % (4 * d["vw"]) != 0:
         return False
+    if op == lift.OP_GEMV and d["tree"] == 3 and N % 256 != 0:     # tensor-copy staging
+        return False
     return not (op == lift.OP_GEMV and d["stages"] > 0 and (N == 0 or N % 4 != 0))
 
 

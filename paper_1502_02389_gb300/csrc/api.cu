@@ -94,6 +94,7 @@ static lift_status init_device(int device) {
 // registry
 // ---------------------------------------------------------------------------
 void register_gemv_tma(std::vector<Variant>& gemv);   // gemv_tma.cu
+void register_gemv_tmap(std::vector<Variant>& gemv);  // gemv_tma.cu (tensor-copy forms)
 void register_reduce_f32(std::vector<Variant>& asum, std::vector<Variant>& dot,
                          std::vector<Variant>& nrm2, std::vector<Variant>& sum);  // reduce_f32.cu
 void register_axpy(std::vector<Variant>& axpy);       // scal_gemv.cu
@@ -117,6 +118,7 @@ static void build_registry() {
   register_gemv(g_ops[LIFT_OP_GEMV]);
   register_gemv_tma(g_ops[LIFT_OP_GEMV]);
   register_gemv_split(g_ops[LIFT_OP_GEMV]);
+  register_gemv_tmap(g_ops[LIFT_OP_GEMV]);
   register_mixed(g_ops);
   register_axpy(g_ops[LIFT_OP_AXPY]);
   register_gemv_t(g_ops[LIFT_OP_GEMV_T]);
@@ -256,6 +258,8 @@ static bool eligible(int op, const Variant& v, const Args& a) {
   if (op == LIFT_OP_BLACKSCHOLES) ok = ok && ptr_ok(a.result, al);   // the put array
   if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) ok = ok && ((a.lda * 4) % al == 0);
   if (op == LIFT_OP_GEMV && v.info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
+  // tensor copies: whole 256-float runs per row, 16-byte row strides
+  if (op == LIFT_OP_GEMV && v.info.tree == 3) ok = ok && a.N % 256 == 0 && a.lda % 4 == 0;
   return ok;
 }
 

@@ -13,15 +13,38 @@
 // counts the consumer warps that have read it.  Requires A and x 16-byte
 // aligned, lda and N multiples of 4 (the library uses the 4-byte-load kernel
 // otherwise).
+//
+// With TMAP the producer moves a stage's WARPS row segments in one tensor
+// copy (cp.async.bulk.tensor.3d) instead of one bulk copy per row: A is
+// described to the copy engine as a 3-D tensor -- 256-float runs, the runs
+// of a row, the rows (strides 1 KiB and lda * 4 bytes) -- and a stage is the
+// box {256, C / 256, WARPS} at run C / 256 * chunk, row r0: the same
+// [WARPS][C] layout in shared memory.  Rows past M and runs past N read as
+// zeros; the box always lands whole, so a stage expects its full size.  It
+// also needs N a multiple of 256.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lift_internal.cuh"
 
 namespace lift {
 namespace {
 
-template <int WARPS, int C, int S>
+// one tensor copy of box {256, C/256, WARPS} at (0, run, row) into dst
+__device__ __forceinline__ void tensor_g2s(void* dst, const CUtensorMap* map, int run, int row,
+                                           uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(run), "r"(row), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int WARPS, int C, int S, bool TMAP>
 __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
     gemv_tma(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
-             const float* __restrict__ x, float beta, float* __restrict__ y, int* status) {
+             const float* __restrict__ x, float beta, float* __restrict__ y, int* status,
+             const __grid_constant__ CUtensorMap amap) {
   static_assert(C % 128 == 0, "a chunk holds whole 32-lane x float4 rows");
   constexpr int kStageFloats = WARPS * C + C;   // row segments, then x
   constexpr int J = C / 128;                    // float4 per lane per chunk
@@ -62,9 +85,15 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
         const uint32_t bytes = static_cast<uint32_t>(cw * sizeof(float));
         const int nrows = static_cast<int>(r_end - r0 < WARPS ? r_end - r0 : WARPS);
         float* st = buf + (size_t)s * kStageFloats;
-        mbar_arrive_expect_tx(&full_bar[s], (nrows + 1) * bytes);
-        for (int r = 0; r < nrows; ++r)
-          bulk_g2s(st + r * C, A + (r0 + r) * lda + c0, bytes, &full_bar[s]);
+        if constexpr (TMAP) {
+          mbar_arrive_expect_tx(&full_bar[s], (uint32_t)(WARPS * C * sizeof(float)) + bytes);
+          tensor_g2s(st, &amap, static_cast<int>(ch * (C / 256)), static_cast<int>(r0),
+                     &full_bar[s]);
+        } else {
+          mbar_arrive_expect_tx(&full_bar[s], (nrows + 1) * bytes);
+          for (int r = 0; r < nrows; ++r)
+            bulk_g2s(st + r * C, A + (r0 + r) * lda + c0, bytes, &full_bar[s]);
+        }
         bulk_g2s(st + WARPS * C, x + c0, bytes, &full_bar[s]);
       }
     }
@@ -115,9 +144,39 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
   }
 }
 
-template <int WARPS, int C, int S>
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+template <int WARPS, int C, int S, bool TMAP>
 struct GemvTma {
-  static const void* kernel() { return reinterpret_cast<const void*>(&gemv_tma<WARPS, C, S>); }
+  static_assert(!TMAP || (C % 256 == 0 && C / 256 <= 256 && WARPS <= 256), "tensor box");
+  static const void* kernel() {
+    return reinterpret_cast<const void*>(&gemv_tma<WARPS, C, S, TMAP>);
+  }
+  // A as the 3-D tensor {256, N / 256, M} (strides 1 KiB, lda * 4 bytes)
+  static lift_status encode(const Args& a, CUtensorMap* m) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return set_error(LIFT_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    const cuuint64_t dims[3] = {256, (cuuint64_t)(a.N / 256), (cuuint64_t)a.M};
+    const cuuint64_t strides[2] = {256 * sizeof(float), (cuuint64_t)a.lda * sizeof(float)};
+    const cuuint32_t box[3] = {256, C / 256, WARPS};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(a.A), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? LIFT_OK : set_error(LIFT_ERR_CUDA, "tensor map encoding failed");
+  }
   static size_t smem() { return (size_t)S * (WARPS * C + C) * sizeof(float); }
   static int64_t grid(const Variant&, const Args& a) {
     int64_t g = persistent_grid(kernel(), (WARPS + 1) * kWarp, smem(), 1);
@@ -132,21 +191,29 @@ struct GemvTma {
     const float* x = static_cast<const float*>(a.x);
     float* y = a.out;
     int* status = current_state()->ws.status;
-    void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &status};
+    alignas(64) CUtensorMap amap{};
+    if constexpr (TMAP) {
+      // the tensor form needs whole 256-float runs and 16-byte row strides
+      if (a.N % 256 != 0 || a.lda % 4 != 0)
+        return set_error(LIFT_ERR_UNSUPPORTED, "tensor-map gemv: N % 256 or lda % 4");
+      const lift_status rc = encode(a, &amap);
+      if (rc != LIFT_OK) return rc;
+    }
+    void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &status, &amap};
     return launch_config(kernel(), dim3((unsigned)g), dim3((WARPS + 1) * kWarp), smem(), 1, s, args);
   }
 };
 
-template <int WARPS, int C, int S>
+template <int WARPS, int C, int S, bool TMAP = false>
 Variant gemv_tma_variant(const char* name) {
-  using K = GemvTma<WARPS, C, S>;
+  using K = GemvTma<WARPS, C, S, TMAP>;
   Variant v{};
   v.info.op = LIFT_OP_GEMV;
   v.info.tile = C;
   v.info.vw = 4;
   v.info.threads = (WARPS + 1) * kWarp;
   v.info.stride = 1;
-  v.info.tree = 0;
+  v.info.tree = TMAP ? 3 : 0;     // 3: staged by tensor copies (needs N % 256 == 0)
   v.info.cluster = 1;
   v.info.passes = 1;
   v.info.stages = S;
@@ -170,6 +237,16 @@ void register_gemv_tma(std::vector<Variant>& L) {
   L.push_back(gemv_tma_variant<4, 1024, 6>("tma_w4_c1024_s6"));
   L.push_back(gemv_tma_variant<8, 1024, 3>("tma_w8_c1024_s3"));
   L.push_back(gemv_tma_variant<16, 512, 6>("tma_w16_c512_s6"));
+  for (size_t i = first; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
+}
+
+// the tensor-copy forms (appended after every other gemv variant, so that the
+// ids of the others stay those the timing data and the cost model know)
+void register_gemv_tmap(std::vector<Variant>& L) {
+  const size_t first = L.size();
+  L.push_back(gemv_tma_variant<8, 1024, 3, true>("tmap_w8_c1024_s3"));
+  L.push_back(gemv_tma_variant<8, 2048, 2, true>("tmap_w8_c2048_s2"));
+  L.push_back(gemv_tma_variant<16, 1024, 2, true>("tmap_w16_c1024_s2"));
   for (size_t i = first; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 

@@ -248,7 +248,7 @@ def test_gemv_all_variants_full_size_sampled_rows(L, shape):
 
 
 @pytest.mark.parametrize("M,N", [(1, 1), (7, 33), (40, 257), (129, 1000), (33, 4100), (5, 8192),
-                                 (3, 50000), (2, 300004)])
+                                 (3, 50000), (2, 300004), (9, 512), (40, 1280), (37, 2304)])
 def test_gemv_bit_exact_to_expression(L, M, N):
     rng = np.random.default_rng(M * N)
     A = rng.standard_normal((M, N)).astype(np.float32)
@@ -258,7 +258,8 @@ def test_gemv_bit_exact_to_expression(L, M, N):
         v = L.lift_variant_describe(L.OP_GEMV, vid)
         # rows whose pitch (lda * 4 bytes) is not a multiple of the vector
         # load run the 4-byte form (variant 0)
-        runs = v if (4 * N) % (4 * v["vw"]) == 0 else L.lift_variant_describe(L.OP_GEMV, 0)
+        ok = (4 * N) % (4 * v["vw"]) == 0 and not (v["tree"] == 3 and N % 256 != 0)
+        runs = v if ok else L.lift_variant_describe(L.OP_GEMV, 0)
         if runs["name"].startswith("gemv_split_"):
             seg, S = L.lift_gemv_segments(runs["id"], M, N)
             ze = ll.gemv_split_z_variant(M, N, 1.25, runs["vw"], runs["threads"], seg, S)

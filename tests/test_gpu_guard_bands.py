@@ -60,7 +60,8 @@ def test_vector_outputs(L, n, off):
         assert intact(bc, n, off) and intact(bp, n, off), ("blackscholes", vid)
 
 
-@pytest.mark.parametrize("M,N,off", [(1, 1, 0), (37, 1030, 1), (3000, 64, 2), (5, 70000, 0)])
+@pytest.mark.parametrize("M,N,off", [(1, 1, 0), (37, 1030, 1), (3000, 64, 2), (5, 70000, 0),
+                                     (37, 1280, 0), (11, 512, 0)])
 def test_matrix_outputs(L, M, N, off):
     A = vec(M * N, 2)
     for op, rows, cols, call in ((L.OP_GEMV, M, N, L.lift_gemv_v), (L.OP_GEMV_T, N, M, L.lift_gemv_t_v)):
