@@ -8,6 +8,13 @@
  *   dot(x, y)           = reduce(add, 0) . map(mult) . zip(x, y)   Fig. 5
  *   gemv(A, x, y, a, b) = y <- a*A*x + b*y, map(dot) over rows     Fig. 5, Sec. 5.1
  *
+ * and, built the same way: the mixed-precision asum / dot (bf16, fp8-e4m3
+ * with block scales), the compensated fp32 asum / dot, nrm2, sum and axpy
+ * (other user functions in the same patterns, Sec. 4.2), gemv-T (gemv over
+ * the reorder-stride transpose, Sec. 3.2), BlackScholes (the map of Fig. 6),
+ * a batched persistent launch of many asum / dot / scal / gemv calls, and
+ * the variant policies (a tuned table and a learned cost model).
+ *
  * Each kernel variant is one low-level expression derived from these with
  * the rewrite rules of Fig. 3 and Fig. 4; its integer parameters (split
  * tile, vector width, reorder-stride, tree depth, combine passes, staging)
@@ -58,8 +65,10 @@ typedef enum {
 
 typedef enum { LIFT_F32 = 0, LIFT_BF16 = 1, LIFT_FP8_E4M3 = 2 } lift_dtype;
 
-/* Operation ids: the four Fig. 5 programs, then the mixed-precision
- * reductions (stored bf16 or fp8-e4m3 inputs). */
+/* Operation ids: the four Fig. 5 programs, the mixed-precision reductions
+ * (stored bf16 or fp8-e4m3 inputs), the user-function programs, gemv-T,
+ * BlackScholes and the compensated fp32 reductions.  Each has its own list
+ * of variants (lift_variant_count / lift_variant_describe). */
 typedef enum {
   LIFT_OP_ASUM = 0,
   LIFT_OP_DOT = 1,
