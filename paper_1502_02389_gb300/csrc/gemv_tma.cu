@@ -240,13 +240,21 @@ void register_gemv_tma(std::vector<Variant>& L) {
   for (size_t i = first; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 
-// the tensor-copy forms (appended after every other gemv variant, so that the
-// ids of the others stay those the timing data and the cost model know)
+// variants added after the first sweeps: the tensor-copy forms and smaller
+// rings (appended after every other gemv variant, so that the ids of the
+// others stay those the timing data and the cost model know)
 void register_gemv_tmap(std::vector<Variant>& L) {
   const size_t first = L.size();
   L.push_back(gemv_tma_variant<8, 1024, 3, true>("tmap_w8_c1024_s3"));
   L.push_back(gemv_tma_variant<8, 2048, 2, true>("tmap_w8_c2048_s2"));
   L.push_back(gemv_tma_variant<16, 1024, 2, true>("tmap_w16_c1024_s2"));
+  // smaller rings: two or three CTAs per SM, each streaming its own rows
+  L.push_back(gemv_tma_variant<8, 1024, 2>("tma_w8_c1024_s2"));
+  L.push_back(gemv_tma_variant<4, 2048, 2>("tma_w4_c2048_s2"));
+  L.push_back(gemv_tma_variant<4, 1024, 3>("tma_w4_c1024_s3"));
+  L.push_back(gemv_tma_variant<2, 2048, 3>("tma_w2_c2048_s3"));
+  L.push_back(gemv_tma_variant<4, 2048, 3>("tma_w4_c2048_s3"));
+  L.push_back(gemv_tma_variant<4, 4096, 2>("tma_w4_c4096_s2"));
   for (size_t i = first; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 
