@@ -913,8 +913,9 @@ METRIC = "HBM GB/s (frac of peak) for asum/dot/gemv; learned vs autotuned varian
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000,
+                    help="timed steps (the default keeps the dot + scal region near 0.3 s, long enough for several clock samples)")
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dot_scal", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")

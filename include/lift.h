@@ -298,13 +298,18 @@ lift_status lift_gemv_v(int variant, int64_t M, int64_t N, float alpha, const fl
  *  cluster  CTAs per cluster (1 = none)
  *  passes   1: last-CTA combine in the same launch; 2: second kernel
  *  stages   0: direct vector loads; k >= 2: k-deep TMA bulk-copy ring
- *  rows     gemv: rows per warp-group step (0 otherwise)
+ *  rows     gemv: rows per warp-group step; gemv-T, compensated, mixed
+ *           precision, BlackScholes: loads (rows) in flight per work-item
  *  lanes    gemv: threads that share one row (0 otherwise)
  *  final_threads  threads of the FP64 final combine
+ *  grid     maps (scal, axpy, BlackScholes): 1 = one CTA per tile, the
+ *           grid covers every tile and the hardware deals CTAs to SMs as
+ *           earlier ones finish; 0 = a persistent grid (at most the
+ *           resident CTAs) that takes the tiles round robin
  */
 typedef struct {
   int op, id, tile, vw, threads, stride, tree, cluster, passes, stages, rows, lanes,
-      final_threads;
+      final_threads, grid;
   char name[64];
 } lift_variant_info;
 

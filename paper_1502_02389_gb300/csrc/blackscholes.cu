@@ -29,7 +29,8 @@
 //
 // Lowering: the rule map(f) -> asScalar . map(vect^VW(f)) . asVector^VW
 // (Fig. 4e), map-workgroup over tiles of THREADS*U vectors dealt round robin
-// to a persistent grid, map-local over the vectors of a tile.  Every variant
+// to a persistent grid (or, GRID == 1, one CTA per tile, dealt to the SMs by
+// the hardware), map-local over the vectors of a tile.  Every variant
 // with the same CND applies the same per-element function with explicitly
 // rounded operations (no contraction), so they agree bit for bit.
 #include <math.h>
@@ -156,13 +157,15 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-template <int THREADS, int VW, int U, int CND>
+template <int THREADS, int VW, int U, int CND, int GRID = 0>
 struct BlackScholes {
   static const void* kernel() { return reinterpret_cast<const void*>(&bs_map<THREADS, VW, U, CND>); }
+  // one CTA per THREADS * U vectors (GRID == 1; the grid-stride loop still
+  // covers every vector if the grid is capped), or at most the resident CTAs
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t per = (int64_t)THREADS * U;
     const int64_t need = (a.n / VW + per - 1) / per;
-    int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
+    int64_t g = GRID == 1 ? INT32_MAX : persistent_grid(kernel(), THREADS, 0, 1);
     if (need < g) g = need;
     return g < 1 ? 1 : g;
   }
@@ -193,9 +196,9 @@ struct BlackScholes {
 // per CND, the id of its 4-byte-load variant (the guarded form)
 constexpr int kFallback[3] = {0, 2, 5};
 
-template <int THREADS, int VW, int U, int CND>
+template <int THREADS, int VW, int U, int CND, int GRID = 0>
 Variant bs_variant(const char* name) {
-  using K = BlackScholes<THREADS, VW, U, CND>;
+  using K = BlackScholes<THREADS, VW, U, CND, GRID>;
   Variant v{};
   v.info.op = LIFT_OP_BLACKSCHOLES;
   v.info.tile = THREADS * VW * U;
@@ -206,6 +209,7 @@ Variant bs_variant(const char* name) {
   v.info.passes = 1;
   v.info.rows = U;
   v.info.lanes = 1;
+  v.info.grid = GRID;
   snprintf(v.info.name, sizeof(v.info.name), "blackscholes_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
@@ -228,6 +232,12 @@ void register_blackscholes(std::vector<Variant>& L) {
   L.push_back(bs_variant<256, 4, 2, 2>("t256_v4_u2_fast"));
   L.push_back(bs_variant<128, 4, 4, 2>("t128_v4_u4_fast"));
   L.push_back(bs_variant<256, 8, 1, 2>("t256_v8_u1_fast"));
+  // one CTA per tile (appended: earlier ids are stable)
+  L.push_back(bs_variant<256, 4, 1, 2, 1>("t256_v4_u1_fast_pertile"));
+  L.push_back(bs_variant<256, 4, 2, 2, 1>("t256_v4_u2_fast_pertile"));
+  L.push_back(bs_variant<128, 4, 4, 2, 1>("t128_v4_u4_fast_pertile"));
+  L.push_back(bs_variant<256, 8, 1, 2, 1>("t256_v8_u1_fast_pertile"));
+  L.push_back(bs_variant<256, 4, 2, 1, 1>("t256_v4_u2_as_pertile"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 

@@ -3,7 +3,10 @@
 //
 // scal = join . map-workgroup(asScalar . map-local(vect^VW(mult(alpha)))
 //                             . asVector^VW) . split^TILE, tiles round robin
-// over a persistent grid.  One correctly rounded fp32 multiply per element
+// over a persistent grid, or (GRID == 1) one work-group per tile, launched
+// all at once and dealt to the SMs by the hardware as earlier ones finish:
+// the same expression, scheduled the way an OpenCL global size of n would
+// be.  One correctly rounded fp32 multiply per element
 // (__fmul_rn), so the output is bit-exact whatever the variant.  STAGES >= 2
 // stages tiles through a TMA bulk-copy ring, multiplies in shared memory and
 // writes back with bulk shared->global copies.
@@ -121,8 +124,24 @@ __global__ void __launch_bounds__(THREADS)
     scal_tail<THREADS, TILE, 4>(n, alpha, x, y, full);
 }
 
-template <int THREADS, int TILE, int VW, int STAGES>
+// Grid of a map over T tiles: one CTA per tile (GRID == 1; the kernels'
+// tile loops then run once, and a grid capped at 2^31 - 1 still covers every
+// tile), or a persistent grid with the same number of tiles for every CTA.
+template <int GRID>
+int64_t map_grid(const void* kernel, int threads, size_t smem, int64_t T) {
+  if constexpr (GRID == 1) {
+    return T < INT32_MAX ? T : INT32_MAX;
+  } else {
+    const int64_t g = persistent_grid(kernel, threads, smem, 1);
+    if (g <= 0) return 0;
+    const int64_t per = (T + g - 1) / g;
+    return (T + per - 1) / per;
+  }
+}
+
+template <int THREADS, int TILE, int VW, int STAGES, int GRID = 0>
 struct Scal {
+  static_assert(GRID == 0 || STAGES == 0, "a staged ring needs several tiles per CTA");
   static const void* kernel() {
     if constexpr (STAGES == 0)
       return reinterpret_cast<const void*>(&scal_ldg<THREADS, TILE, VW>);
@@ -130,13 +149,9 @@ struct Scal {
       return reinterpret_cast<const void*>(&scal_tma<THREADS, TILE, STAGES>);
   }
   static size_t smem() { return (size_t)STAGES * TILE * sizeof(float); }
-  // persistent grid with the same number of tiles for every CTA
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t T = a.n > 0 ? (a.n + TILE - 1) / TILE : 1;
-    const int64_t g = persistent_grid(kernel(), THREADS, smem(), 1);
-    if (g <= 0) return 0;
-    const int64_t per = (T + g - 1) / g;
-    return (T + per - 1) / per;
+    return map_grid<GRID>(kernel(), THREADS, smem(), T);
   }
   static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
     const int64_t g = grid(v, a);
@@ -156,9 +171,9 @@ struct Scal {
   }
 };
 
-template <int THREADS, int TILE, int VW, int STAGES>
+template <int THREADS, int TILE, int VW, int STAGES, int GRID = 0>
 Variant scal_variant(const char* name) {
-  using K = Scal<THREADS, TILE, VW, STAGES>;
+  using K = Scal<THREADS, TILE, VW, STAGES, GRID>;
   Variant v{};
   v.info.op = LIFT_OP_SCAL;
   v.info.tile = TILE;
@@ -169,6 +184,7 @@ Variant scal_variant(const char* name) {
   v.info.cluster = 1;
   v.info.passes = 1;
   v.info.stages = STAGES;
+  v.info.grid = GRID;
   snprintf(v.info.name, sizeof(v.info.name), "scal_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
@@ -214,15 +230,12 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-template <int THREADS, int TILE, int VW>
+template <int THREADS, int TILE, int VW, int GRID = 0>
 struct Axpy {
   static const void* kernel() { return reinterpret_cast<const void*>(&axpy_ldg<THREADS, TILE, VW>); }
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t T = a.n > 0 ? (a.n + TILE - 1) / TILE : 1;
-    const int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
-    if (g <= 0) return 0;
-    const int64_t per = (T + g - 1) / g;
-    return (T + per - 1) / per;
+    return map_grid<GRID>(kernel(), THREADS, 0, T);
   }
   static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
     const int64_t g = grid(v, a);
@@ -236,9 +249,9 @@ struct Axpy {
   }
 };
 
-template <int THREADS, int TILE, int VW>
+template <int THREADS, int TILE, int VW, int GRID = 0>
 Variant axpy_variant(const char* name) {
-  using K = Axpy<THREADS, TILE, VW>;
+  using K = Axpy<THREADS, TILE, VW, GRID>;
   Variant v{};
   v.info.op = LIFT_OP_AXPY;
   v.info.tile = TILE;
@@ -247,6 +260,7 @@ Variant axpy_variant(const char* name) {
   v.info.stride = 1;
   v.info.cluster = 1;
   v.info.passes = 1;
+  v.info.grid = GRID;
   snprintf(v.info.name, sizeof(v.info.name), "axpy_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
@@ -406,6 +420,11 @@ void register_scal(std::vector<Variant>& L) {
   L.push_back(scal_variant<256, 4096, 4, 4>("t4096_tma4"));
   L.push_back(scal_variant<256, 4096, 4, 2>("t4096_tma2"));
   L.push_back(scal_variant<256, 4096, 4, 6>("t4096_tma6"));
+  // one CTA per tile (appended: earlier ids are stable)
+  L.push_back(scal_variant<256, 2048, 4, 0, 1>("t2048_v4_ldg_pertile"));
+  L.push_back(scal_variant<256, 4096, 4, 0, 1>("t4096_v4_ldg_pertile"));
+  L.push_back(scal_variant<256, 4096, 8, 0, 1>("t4096_v8_ldg_pertile"));
+  L.push_back(scal_variant<256, 8192, 8, 0, 1>("t8192_v8_ldg_pertile"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 
@@ -415,6 +434,9 @@ void register_axpy(std::vector<Variant>& L) {
   L.push_back(axpy_variant<256, 2048, 4>("t2048_v4_ldg"));
   L.push_back(axpy_variant<256, 4096, 4>("t4096_v4_ldg"));
   L.push_back(axpy_variant<256, 2048, 8>("t2048_v8_ldg"));
+  L.push_back(axpy_variant<256, 2048, 4, 1>("t2048_v4_ldg_pertile"));
+  L.push_back(axpy_variant<256, 4096, 4, 1>("t4096_v4_ldg_pertile"));
+  L.push_back(axpy_variant<256, 4096, 8, 1>("t4096_v8_ldg_pertile"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 

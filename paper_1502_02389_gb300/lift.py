@@ -46,7 +46,7 @@ class OpDesc(ctypes.Structure):
 class VariantInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in ("op", "id", "tile", "vw", "threads", "stride", "tree",
                                            "cluster", "passes", "stages", "rows", "lanes",
-                                           "final_threads")] + [("name", ctypes.c_char * 64)]
+                                           "final_threads", "grid")] + [("name", ctypes.c_char * 64)]
 
 
 _P = ctypes.c_void_p
