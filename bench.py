@@ -146,6 +146,24 @@ def job_rate(bytes_per_rank_step: float, steps: int, world: int, max_ms: float) 
     return world * bytes_per_rank_step * steps / (max_ms / 1e3) / 1e9
 
 
+BATCH_SCHEDULES = {"queue": 0, "per-item": 1}    # LIFT_BATCH_QUEUE, LIFT_BATCH_PER_ITEM
+
+
+def batch_create(args, descs):
+    """lift_batch_create, then the --batch-schedule choice (if any)."""
+    from paper_1502_02389_gb300 import lift
+    h = lift.lift_batch_create(descs)
+    if getattr(args, "batch_schedule", None):
+        lift.lift_batch_set_schedule(h, BATCH_SCHEDULES[args.batch_schedule])
+    return h
+
+
+def schedule_name(h):
+    from paper_1502_02389_gb300 import lift
+    k = lift.lift_batch_schedule(h)
+    return {v: n for n, v in BATCH_SCHEDULES.items()}.get(k, str(k))
+
+
 class Clocks:
     """nvidia-smi sampling (every 100 ms) around and during the timed
     region.  The sampler is started, and its first sample awaited, before
@@ -267,7 +285,7 @@ def run_ours(args, rank, world, dist):
         pd = lift.lift_variant_describe(lift.OP_DOT, vd)
         ps = lift.lift_variant_describe(lift.OP_SCAL, vs)
         bytes_step = 16 * n
-        hb2 = lift.lift_batch_create([
+        hb2 = batch_create(args, [
             {"op": lift.OP_DOT, "variant": vd, "n": n, "x": x, "y": y, "out": r},
             {"op": lift.OP_SCAL, "variant": vs, "n": n, "alpha": float(alpha), "x": x, "out": z}])
 
@@ -318,7 +336,7 @@ def run_ours(args, rank, world, dist):
         C = E2E_CHUNKS
         chunk = n // C
         rparts = torch.zeros(C, device=dev)
-        hbc = [lift.lift_batch_create([
+        hbc = [batch_create(args, [
             {"op": lift.OP_DOT, "variant": vd, "n": chunk, "x": x[c * chunk:(c + 1) * chunk],
              "y": y[c * chunk:(c + 1) * chunk], "out": rparts[c:c + 1]},
             {"op": lift.OP_SCAL, "variant": vs, "n": chunk, "alpha": float(alpha),
@@ -356,6 +374,8 @@ def run_ours(args, rank, world, dist):
                                    if args.mode == "batched" else
                                    "two calls (lift_dot_v, lift_scal_v)"),
                   "l2": "no flush: inputs 3 x 256 MiB exceed the 129 MB L2"}
+        if args.mode == "batched":
+            config["batch_schedule"] = schedule_name(hb2)
     elif wl == "mixed":
         n = WORKLOADS[wl]["n"]
         xv, yv = synth.mixed_values(n)
@@ -541,7 +561,7 @@ def run_ours(args, rank, world, dist):
         handles = {}
         for name, (pol, path) in policies.items():
             lift.lift_set_policy(pol, path)
-            handles[name] = lift.lift_batch_create(descs)
+            handles[name] = batch_create(args, descs)
         lift.lift_set_policy(lift.POLICY_FIXED)
         main_policy = "mlp" if "mlp" in handles else "fixed"
         hb = handles[main_policy]
@@ -577,7 +597,7 @@ def run_ours(args, rank, world, dist):
 
         e2e_step, host, h2d, d2h = None, {}, 0, 0
         config = {"workload": WORKLOADS[wl]["desc"], "ops": len(ops), "items": info["items"],
-                  "grid": info["grid"], "policy": main_policy,
+                  "grid": info["grid"], "policy": main_policy, "batch_schedule": schedule_name(hb),
                   "l2": "no flush: every run reads about 60 GB, far beyond the 129 MB L2"}
     else:
         M, N = WORKLOADS[wl]["M"], WORKLOADS[wl]["N"]
@@ -919,6 +939,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dot_scal", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-schedule", default=None, choices=sorted(BATCH_SCHEDULES),
+                    help="how batch work items meet the SMs (default: the library's)")
     ap.add_argument("--mlp", default=None, help="cost-model weights for the batch workload")
     ap.add_argument("--variant", action="append",
                     help="force a variant by name (repeatable), e.g. for a profiling capture")

@@ -418,7 +418,21 @@ typedef struct lift_batch lift_batch;
 
 lift_status lift_batch_create(const lift_op_desc* ops, int64_t count, lift_batch** batch);
 lift_status lift_batch_run(lift_batch* batch, void* stream);
-/* Work items, algorithmic bytes of one run, and CTAs of the persistent grid. */
+/* How the work items meet the SMs (map-workgroup over the items, two
+ * schedules of the same expression; results are identical):
+ *   LIFT_BATCH_QUEUE     a persistent grid (SMs x resident CTAs) whose CTAs
+ *                        pop queue positions with an atomic (the default);
+ *   LIFT_BATCH_PER_ITEM  one CTA per work item, CTA q taking queue position
+ *                        q, dealt to the SMs by the hardware as earlier CTAs
+ *                        retire (LIFT_ERR_UNSUPPORTED beyond 2^31 - 1 items).
+ * A change takes effect at the next lift_batch_run (the graph is captured
+ * again); do not call it while a run of the batch is in flight. */
+#define LIFT_BATCH_QUEUE 0
+#define LIFT_BATCH_PER_ITEM 1
+lift_status lift_batch_set_schedule(lift_batch* batch, int schedule);
+/* The batch's schedule (-1 for a NULL batch). */
+int lift_batch_schedule(const lift_batch* batch);
+/* Work items, algorithmic bytes of one run, and CTAs of the launch. */
 lift_status lift_batch_info(const lift_batch* batch, int64_t* items, int64_t* bytes, int64_t* grid);
 /* For op i: the variant the batch adopted, the processing mode it maps to
  * (vector ops: 0..5 = (vector width, vectors per thread per tile) of

@@ -106,6 +106,8 @@ _SIGS = {
     "lift_axpy_v": ([ctypes.c_int, _I64, ctypes.c_float, _P, _P, _P], ctypes.c_int),
     "lift_batch_create": ([ctypes.c_void_p, _I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "lift_batch_run": ([_P, _P], ctypes.c_int),
+    "lift_batch_set_schedule": ([_P, ctypes.c_int], ctypes.c_int),
+    "lift_batch_schedule": ([_P], ctypes.c_int),
     "lift_batch_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
                         ctypes.c_int),
     "lift_batch_op_choice": ([_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -413,6 +415,18 @@ def lift_batch_create(descs) -> int:
 
 def lift_batch_run(batch, stream=None):
     _check(lib().lift_batch_run(batch, _stream(stream)), "lift_batch_run")
+
+
+BATCH_QUEUE = 0
+BATCH_PER_ITEM = 1
+
+
+def lift_batch_set_schedule(batch, schedule: int):
+    _check(lib().lift_batch_set_schedule(batch, int(schedule)), "lift_batch_set_schedule")
+
+
+def lift_batch_schedule(batch) -> int:
+    return int(lib().lift_batch_schedule(batch))
 
 
 def lift_batch_info(batch):

@@ -97,6 +97,9 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     with pytest.raises(lift.LiftError) as e:
         lift.lift_asum_ex(lift.BF16, 4096, 8192, 10, 64, None, 0)  # bf16 takes no scales
     assert e.value.status == lift.ERR_INVALID_ARG
+    with pytest.raises(lift.LiftError) as e:
+        lift.lift_batch_set_schedule(None, lift.BATCH_PER_ITEM)   # no batch
+    assert e.value.status == lift.ERR_INVALID_ARG
 
 
 def test_batch_create_rejects_bad_descriptors_before_any_device_work(lib):

@@ -117,12 +117,16 @@ def read_out(L, d, data):
     return data["outbuf"].cpu().numpy()
 
 
-def test_small_batch_bit_exact_and_replayable(L):
+@pytest.mark.parametrize("schedule", [0, 1])      # LIFT_BATCH_QUEUE, LIFT_BATCH_PER_ITEM
+def test_small_batch_bit_exact_and_replayable(L, schedule):
     descs, datas, keep = make_small_batch(L)
     h = L.lift_batch_create(descs)
     try:
+        L.lift_batch_set_schedule(h, schedule)
         info = L.lift_batch_info(h)
         assert info["items"] >= len(descs) - sum(1 for d in descs if d["op"] == L.OP_SCAL and d["n"] == 0)
+        if schedule == L.BATCH_PER_ITEM:
+            assert info["grid"] == info["items"]
         for rep in range(2):
             if rep:   # gemv updates y in place: restore it before the replay
                 for d, data in zip(descs, datas):
@@ -140,6 +144,32 @@ def test_small_batch_bit_exact_and_replayable(L):
                 if d["op"] == L.OP_ASUM and d["n"]:
                     ref = blas.asum(data["x"].astype(np.float64))
                     assert abs(float(got[0]) - ref) <= blas.tolerance(d["n"], blas.asum_terms(data["x"]))
+    finally:
+        L.lift_batch_destroy(h)
+
+
+def test_schedules_agree_bit_for_bit(L):
+    """The two schedules of the batch (queue and one CTA per item) are the
+    same expression: switching between runs of one batch re-captures its
+    graph and leaves every output bit unchanged."""
+    descs, datas, keep = make_small_batch(L, seed=5)
+    h = L.lift_batch_create(descs)
+    outs = []
+    try:
+        for schedule in (L.BATCH_QUEUE, L.BATCH_PER_ITEM, L.BATCH_QUEUE):
+            for d, data in zip(descs, datas):
+                if d["op"] == L.OP_GEMV:
+                    d["out"].copy_(torch.from_numpy(data["out0"]))
+            L.lift_batch_set_schedule(h, schedule)
+            L.lift_batch_run(h)
+            torch.cuda.synchronize()
+            outs.append([read_out(L, d, data).copy() for d, data in zip(descs, datas)])
+        for a, b in zip(outs[0], outs[1]):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+        for a, b in zip(outs[0], outs[2]):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+        with pytest.raises(L.LiftError):
+            L.lift_batch_set_schedule(h, 2)
     finally:
         L.lift_batch_destroy(h)
 
