@@ -101,6 +101,7 @@ void register_axpy(std::vector<Variant>& axpy);       // scal_gemv.cu
 void register_gemv_t(std::vector<Variant>& gemv_t);   // gemv_t.cu
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB);
 void register_gemv_split(std::vector<Variant>& gemv);  // gemv_split.cu
+void register_gemv_pertile(std::vector<Variant>& gemv);  // scal_gemv.cu (one CTA per row group)
 void register_blackscholes(std::vector<Variant>& bs);  // blackscholes.cu
 void register_compensated(std::vector<Variant>& asum, std::vector<Variant>& dot);  // compensated.cu
 void register_reduce_derived(std::vector<Variant>& asum, std::vector<Variant>& dot);  // reduce_derived.cu
@@ -119,6 +120,7 @@ static void build_registry() {
   register_gemv_tma(g_ops[LIFT_OP_GEMV]);
   register_gemv_split(g_ops[LIFT_OP_GEMV]);
   register_gemv_tmap(g_ops[LIFT_OP_GEMV]);
+  register_gemv_pertile(g_ops[LIFT_OP_GEMV]);
   register_mixed(g_ops);
   register_axpy(g_ops[LIFT_OP_AXPY]);
   register_gemv_t(g_ops[LIFT_OP_GEMV_T]);

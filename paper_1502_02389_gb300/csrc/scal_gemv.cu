@@ -353,12 +353,15 @@ __global__ void gemv_scale_y(int64_t M, float beta, float* y) {
     y[i] = (beta == 0.0f) ? 0.0f : __fadd_rn(0.0f, __fmul_rn(beta, y[i]));
 }
 
-template <int WARPS, int VW, int UNROLL>
+// GRID 0: at most the resident CTAs, each warp taking rows round robin;
+// GRID 1: one CTA per WARPS rows (capped at 2^31 - 1 CTAs; the row loop
+// still covers every row), dealt to the SMs by the hardware.
+template <int WARPS, int VW, int UNROLL, int GRID = 0>
 struct Gemv {
   static const void* kernel() { return reinterpret_cast<const void*>(&gemv_warp<WARPS, VW, UNROLL>); }
   static int64_t grid(const Variant&, const Args& a) {
     const int64_t need = (a.M + WARPS - 1) / WARPS;
-    int64_t g = persistent_grid(kernel(), WARPS * kWarp, 0, 1);
+    int64_t g = GRID == 1 ? INT32_MAX : persistent_grid(kernel(), WARPS * kWarp, 0, 1);
     if (need < g) g = need;
     return g < 1 ? 1 : g;
   }
@@ -379,9 +382,9 @@ struct Gemv {
   }
 };
 
-template <int WARPS, int VW, int UNROLL>
+template <int WARPS, int VW, int UNROLL, int GRID = 0>
 Variant gemv_variant(const char* name) {
-  using K = Gemv<WARPS, VW, UNROLL>;
+  using K = Gemv<WARPS, VW, UNROLL, GRID>;
   Variant v{};
   v.info.op = LIFT_OP_GEMV;
   v.info.tile = 0;
@@ -394,6 +397,7 @@ Variant gemv_variant(const char* name) {
   v.info.stages = 0;
   v.info.rows = WARPS;
   v.info.lanes = kWarp;
+  v.info.grid = GRID;
   snprintf(v.info.name, sizeof(v.info.name), "gemv_%s", name);
   v.launch = &K::launch;
   v.grid = &K::grid;
@@ -449,6 +453,17 @@ void register_gemv(std::vector<Variant>& L) {
   L.push_back(gemv_variant<4, 4, 4>("w4_v4_u4"));
   L.push_back(gemv_variant<4, 8, 2>("w4_v8_u2"));
   L.push_back(gemv_variant<16, 4, 4>("w16_v4_u4"));
+  for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
+}
+
+// One CTA per WARPS rows; registered after every other gemv family so that
+// earlier ids stay stable.
+void register_gemv_pertile(std::vector<Variant>& L) {
+  L.push_back(gemv_variant<8, 4, 4, 1>("w8_v4_u4_pertile"));
+  L.push_back(gemv_variant<8, 8, 2, 1>("w8_v8_u2_pertile"));
+  L.push_back(gemv_variant<8, 8, 4, 1>("w8_v8_u4_pertile"));
+  L.push_back(gemv_variant<4, 8, 2, 1>("w4_v8_u2_pertile"));
+  L.push_back(gemv_variant<4, 4, 4, 1>("w4_v4_u4_pertile"));
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }
 
