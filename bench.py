@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import tempfile
 import statistics
 import subprocess
 import sys
@@ -546,7 +547,7 @@ def run_ours(args, rank, world, dist):
                     q[k] = base + 4 * e[k]
             descs.append(q)
         policies = {"fixed": (lift.POLICY_FIXED, None)}
-        table = os.path.join(ROOT, "gpurun_out", "bench_table.txt")
+        table = os.path.join(tempfile.gettempdir(), f"lift_bench_table_{os.getpid()}.txt")
         try:
             from paper_1502_02389_gb300 import tune
             recs = tune.load_csv(os.path.join(costmodel.DATA, "timings_gb300_train.csv"))

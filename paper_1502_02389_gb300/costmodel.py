@@ -7,8 +7,8 @@ train a small network that maps the features of a call (``lift_features``:
 op family, log2 sizes, element type) to one predicted value per kernel
 variant: the log of the variant's time relative to the fastest variant of
 that shape.  The library's MLP policy picks the argmin over the op's
-variants; exhaustive autotuning stays the fallback and the judge of the
-pick's regret t(pick) / t(best).
+variants; exhaustive autotuning stays the fallback and the yardstick of
+the pick's regret t(pick) / t(best).
 
 Training runs on the GPU through the library's own kernels
 (``lift_mlp_forward`` / ``_loss`` / ``_backward`` / ``_adam``); this module
