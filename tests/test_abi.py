@@ -100,6 +100,7 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     with pytest.raises(lift.LiftError) as e:
         lift.lift_batch_set_schedule(None, lift.BATCH_PER_ITEM)   # no batch
     assert e.value.status == lift.ERR_INVALID_ARG
+    assert lift.lift_batch_schedule(None) == -1
 
 
 def test_batch_create_rejects_bad_descriptors_before_any_device_work(lib):
