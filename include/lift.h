@@ -426,7 +426,8 @@ lift_status lift_batch_run(lift_batch* batch, void* stream);
  *                        q, dealt to the SMs by the hardware as earlier CTAs
  *                        retire (LIFT_ERR_UNSUPPORTED beyond 2^31 - 1 items).
  * A change takes effect at the next lift_batch_run (the graph is captured
- * again); do not call it while a run of the batch is in flight. */
+ * again); if the batch has run before, the call first synchronises the
+ * device so that no launch of the old graph is in flight. */
 #define LIFT_BATCH_QUEUE 0
 #define LIFT_BATCH_PER_ITEM 1
 lift_status lift_batch_set_schedule(lift_batch* batch, int schedule);

@@ -518,7 +518,9 @@ lift_status lift_batch_set_schedule(lift_batch* b, int schedule) {
   if (schedule == LIFT_BATCH_PER_ITEM && b->num_items > INT32_MAX)
     return set_error(LIFT_ERR_UNSUPPORTED, "more work items than CTAs in a grid");
   if (schedule == b->schedule) return LIFT_OK;
-  // the next run captures the graph again
+  // the next run captures the graph again; a launch of the old one may still
+  // be in flight on some stream, so let the device drain first
+  if (b->exec) cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
