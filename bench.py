@@ -250,7 +250,12 @@ def run_ours(args, rank, world, dist):
 
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
-    build.build()
+    if local == 0:
+        build.build()            # one builder per node; the other ranks wait for it
+    if dist:
+        dist.barrier()
+    if local != 0:
+        build.build()            # up to date by now: only checks timestamps
     lift.lift_init(local)
     dev = torch.device("cuda", local)
     wl = args.workload
