@@ -56,7 +56,7 @@ WORKLOADS = {
 }
 
 
-E2E_CHUNKS = 8      # slices of the end-to-end pipeline (16 measured slower: 310 vs 348 GB/s)
+E2E_CHUNKS = 8      # slices of the end-to-end pipeline (GB/s of dot + scal: 4 slices 336, 6: 304, 8: 347, 12: 299, 16: 310)
 
 
 def peaks():
