@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import math
 import os
+import time
 from collections import defaultdict
 from typing import Dict, List, Optional, Tuple
 
@@ -264,13 +265,16 @@ def main():
         w = a.workload_weight
         X, T, M = (np.concatenate([A, np.repeat(B, w, axis=0)]) for A, B in ((X, Xw), (T, Tw), (M, Mw)))
     trainer = Trainer(X, T, M, seed=a.seed)
+    t0 = time.perf_counter()
     hist = trainer.train(a.steps, a.lr, log_every=max(1, a.steps // 10))
+    train_s = time.perf_counter() - t0      # train() ends with a device synchronise
     save(a.out, trainer.params(), V, off)
     res = evaluate_policies(tr + wl, ho, a.out, a.out + ".table")
     if wl:
         res["workloads"] = summary(regrets(wl, lambda op, n, M, N: _mlp_pick(a.out, op, n, M, N)))
     res.update({"loss": hist, "train_timings": len(tr), "workload_timings": len(wl),
-                "heldout_timings": len(ho), "train_rows": int(X.shape[0])})
+                "heldout_timings": len(ho), "train_rows": int(X.shape[0]),
+                "train_seconds": round(train_s, 3), "adam_steps": a.steps})
     print(json.dumps(res))
 
 

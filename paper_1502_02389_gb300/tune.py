@@ -20,6 +20,7 @@ import json
 import math
 import os
 import statistics
+import time
 from typing import Dict, Iterable, List, Optional, Tuple
 
 import numpy as np
@@ -230,6 +231,7 @@ def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], r
     pools = Pools()
     out = []
     f = open(db_path, "a") if db_path else None
+    t_start, n_shapes = time.perf_counter(), 0
     try:
         for (op, n, M, N) in shapes:
             vids = variants.get(op) if variants else None
@@ -256,9 +258,14 @@ def sweep(shapes: Iterable[Tuple[int, int, int, int]], db_path: Optional[str], r
                 print(f"{lift.OP_NAMES[op]:10s} n={n} M={M} N={N}: best {best['name']} "
                       f"{best['ms'] * 1e3:.1f} us {best['gbs']:.0f} GB/s", flush=True)
             del buf
+            n_shapes += 1
     finally:
         if f:
             f.close()
+    if verbose and out:
+        wall = time.perf_counter() - t_start
+        print(f"swept {n_shapes} shapes, {len(out)} timings in {wall:.1f} s "
+              f"({wall / max(1, n_shapes):.2f} s per shape)", flush=True)
     assert lift.lift_read_status() == 0, "a kernel reported a device-side timeout"
     return out
 
