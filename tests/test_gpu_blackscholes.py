@@ -1,6 +1,7 @@
 """BlackScholes map (Fig. 6) on the GPU against the FP64 oracle: every
 option of the 4M-price case within the fp32 bound, all variants bit-identical
-to one another, ragged and misaligned inputs, edge cases."""
+to one another, sampled options of the 2^26-price bench case, ragged and
+misaligned inputs, edge cases."""
 import math
 
 import numpy as np
@@ -52,6 +53,30 @@ def test_paper_size_every_option_within_bound(L):
         # same normal-distribution evaluation (info "tree") agree bit for bit
         ref = first.setdefault(info["tree"], (c, p))
         assert np.array_equal(c, ref[0]) and np.array_equal(p, ref[1]), info["name"]
+
+
+def test_bench_size_sampled_policy_pick(L):
+    """The bench's configuration: 2^26 prices through the policy-picked
+    entry point (one CTA per tile: 32,768 CTAs), checked against the oracle
+    on 6,000 sampled options spread over every part of the grid and on the
+    last 1,000, and bit-identical to an explicit persistent variant of the
+    same evaluation on the samples."""
+    n = 1 << 26
+    sh = synth.stock_prices(n)
+    s = torch.from_numpy(sh).cuda()
+    c = torch.full((n,), float("nan"), device="cuda")
+    p = torch.full((n,), float("nan"), device="cuda")
+    L.lift_blackscholes(n, s, K, R, SIG, T, c, p)
+    idx = np.concatenate([np.random.default_rng(11).choice(n - 1000, 6000, replace=False),
+                          np.arange(n - 1000, n)])
+    cg, pg = c.cpu().numpy()[idx], p.cpu().numpy()[idx]
+    cr, pr = finance.black_scholes(sh[idx], K, R, SIG, T)
+    tol = finance.tolerance(sh[idx], K, R, T)
+    assert np.all(np.abs(cg - cr) <= tol) and np.all(np.abs(pg - pr) <= tol)
+    names = {L.lift_variant_describe(L.OP_BLACKSCHOLES, v)["name"]: v
+             for v in range(L.lift_variant_count(L.OP_BLACKSCHOLES))}
+    c2, p2 = run(L, names["blackscholes_t128_v4_u4_fast"], s)
+    assert np.array_equal(c2[idx], cg) and np.array_equal(p2[idx], pg)
 
 
 @pytest.mark.parametrize("n", [1, 3, 7, 1000003])
