@@ -150,3 +150,55 @@ def test_mixed_read_only_their_inputs(L, n, off):
                 name = L.lift_variant_describe(op, vid)["name"]
                 assert np.isfinite(got), (name, n, off)
                 assert abs(got - ref) <= blas.tolerance(n, terms), (name, n, off, got, ref)
+
+
+@pytest.mark.parametrize("schedule", [0, 1])      # LIFT_BATCH_QUEUE, LIFT_BATCH_PER_ITEM
+def test_batch_reads_only_its_inputs(L, schedule):
+    """A batch of asum / dot / gemv ops of ragged sizes and misaligned starts,
+    each operand between NaN words (gemv: and NaN in the lda padding)."""
+    rng = np.random.default_rng(9)
+    descs, checks, keep = [], [], []
+    for i in range(60):
+        kind = i % 3
+        off = i % 4
+        if kind < 2:
+            n = int(rng.choice([1, 31, 4097, 70001, 300003]))
+            x, y = vals(n, 100 + i), vals(n, 200 + i)
+            bx, px = nan_padded(x, off)
+            by, py = nan_padded(y, off)
+            out = torch.full((1,), -1.0, device="cuda")
+            keep += [bx, by, out]
+            d = {"op": L.OP_ASUM if kind == 0 else L.OP_DOT, "variant": -1, "n": n, "x": px,
+                 "out": out}
+            if kind == 0:
+                ref, terms = blas.asum(x.astype(np.float64)), blas.asum_terms(x)
+            else:
+                d["y"] = py
+                ref, terms = blas.dot(x.astype(np.float64), y.astype(np.float64)), blas.dot_terms(x, y)
+            descs.append(d)
+            checks.append((out, ref, blas.tolerance(n, terms)))
+        else:
+            M, N = int(rng.integers(1, 200)), int(rng.choice([1, 33, 128, 1000, 4100]))
+            lda = N + int(rng.choice([0, 3, 8]))
+            A = vals(M * N, 300 + i).reshape(M, N)
+            x, y0 = vals(N, 400 + i), vals(M, 500 + i)
+            bA, pA = padded_matrix(A, lda, off)
+            bx, px = nan_padded(x, off)
+            y = torch.from_numpy(y0.copy()).cuda()
+            keep += [bA, bx, y]
+            descs.append({"op": L.OP_GEMV, "variant": -1, "M": M, "N": N, "lda": lda,
+                          "alpha": 1.0, "beta": 0.5, "A": pA, "x": px, "out": y})
+            ref = blas.gemv(A.astype(np.float64), x.astype(np.float64), y0.astype(np.float64),
+                            1.0, 0.5)
+            checks.append((y, ref, blas.tolerance(N, 1.0) * blas.gemv_row_terms(A, x, y0, 1.0, 0.5)))
+    h = L.lift_batch_create(descs)
+    try:
+        L.lift_batch_set_schedule(h, schedule)
+        L.lift_batch_run(h)
+        torch.cuda.synchronize()
+        for i, (out, ref, tol) in enumerate(checks):
+            got = out.cpu().numpy().astype(np.float64)
+            assert np.all(np.isfinite(got)), i
+            assert np.all(np.abs(got - ref) <= tol), i
+    finally:
+        L.lift_batch_destroy(h)
