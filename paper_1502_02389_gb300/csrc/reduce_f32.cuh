@@ -76,6 +76,9 @@ __device__ __forceinline__ int vec_index(int t, int j) {
 template <int OP, int THREADS, int CLUSTER, bool ONEPASS>
 __device__ __forceinline__ void finish(float r, float* red, double* red64, float* partials,
                                        unsigned* ticket, float* result, double* result64) {
+  // two passes: the combine kernel (a programmatic dependent launch) may be
+  // scheduled now; it waits for this grid to finish before it reads
+  if constexpr (!ONEPASS) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   r = block_tree<THREADS>(r, red);
   int64_t pidx = blockIdx.x;
   bool leader = true;
@@ -263,6 +266,7 @@ __global__ void __launch_bounds__(THREADS)
 template <int OP, int FT>
 __global__ void __launch_bounds__(FT)
     combine_kernel(const float* __restrict__ partials, int64_t P, float* result, double* result64) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // the first pass has finished
   __shared__ double red64[kWarp];
   const double s = post<OP>(combine_partials<FT>(partials, P, red64));
   if (threadIdx.x == 0) {
@@ -272,6 +276,27 @@ __global__ void __launch_bounds__(FT)
 }
 
 constexpr int kCombineThreads = 256;
+
+// The second pass, launched as a programmatic dependent of the first so that
+// its launch overlaps the first pass's tail.
+template <int OP>
+lift_status launch_combine(const float* partials, int64_t P, float* result, double* result64,
+                           cudaStream_t s) {
+  void* args[] = {&partials, &P, &result, &result64};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(kCombineThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cuda_check(cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&combine_kernel<OP, kCombineThreads>),
+                                        args),
+                    "combine launch");
+}
 
 template <int OP, int THREADS, int TILE, int VW, bool STRIDE, int STAGES, int CLUSTER, int PASSES>
 struct ReduceF32 {
@@ -315,10 +340,7 @@ struct ReduceF32 {
     void* args[] = {&x, &y, &n, &partials, &ticket, &result, &result64, &status};
     lift_status rc = launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), CLUSTER, s, args);
     if (rc != LIFT_OK || PASSES == 1) return rc;
-    const int64_t P = g / CLUSTER;
-    combine_kernel<OP, kCombineThreads><<<1, kCombineThreads, 0, s>>>(partials, P, a.result,
-                                                                       a.result64);
-    return cuda_check(cudaGetLastError(), "combine launch");
+    return launch_combine<OP>(partials, g / CLUSTER, a.result, a.result64, s);
   }
 };
 
