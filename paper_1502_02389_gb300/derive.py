@@ -145,6 +145,16 @@ class Pad:
 
 
 @dataclass(frozen=True)
+class ZipWith:
+    """zip of each element (a row) with a captured vector: the dot(x) that
+    gemv maps over the rows of A (Fig. 5)."""
+    name: str
+
+    def __repr__(self) -> str:
+        return f"zip({self.name})"
+
+
+@dataclass(frozen=True)
 class C:
     """Composition fs[0] . fs[1] . ... (the last is applied first)."""
     fs: Tuple[Any, ...]
@@ -370,13 +380,22 @@ WG_SIZES = (32, 64, 128, 256, 512, 1024)
 WIDTHS = (1, 2, 4, 8)
 
 
+GEMV_ROWS = (1, 2, 4, 8, 16, 32)     # rows per work-group (a warp each)
+GEMV_N = 512                          # the row length the gemv derivations are written for
+
+
 def program(op: str):
     """High-level expression of an op (Fig. 5); dot and axpy take the
-    zipped pair of their inputs."""
+    zipped pair of their inputs; gemv's z = join . map(scal(a) . dot(x))
+    over the rows of A."""
     if op in REDUCTIONS:
         return comp(Reduce("reduce", ADD, 0), Map("map", REDUCTIONS[op]))
     if op in MAPS:
         return Map("map", MAPS[op])
+    if op == "gemv":
+        row = comp(Map("map", Fn("mult_by", ("a",))), Reduce("reduce", ADD, 0), Map("map", MULT),
+                   ZipWith("x"))
+        return comp(Join(), Map("map", row))
     raise KeyError(op)
 
 
@@ -491,6 +510,45 @@ def derive_map(op: str, tile: int, vw: int, threads: int, staged: bool) -> Deriv
     return d
 
 
+def derive_gemv(rows: int, vw: int, strided: bool, n: int = GEMV_N) -> Derivation:
+    """One derivation of gemv's z (Fig. 5) for rows of n elements, the form of
+    the warp-per-row kernels: the rows split into work-groups of `rows`,
+    each row's dot done by 32 work-items (a warp; like the 32-groups of a
+    two-level reduction tree, the map over a work-group's rows stays a
+    plain map) that each fold J = n / (32 vw) vectors of the row zipped with
+    x (taken strided or as a contiguous run), then a halving tree over the
+    32 partial sums, then the scaling by a."""
+    J = n // (32 * vw)
+    if J < 1 or J * 32 * vw != n:
+        raise NotApplicable
+    d = Derivation("gemv", program("gemv"), choice=dict(rows=rows, vw=vw, strided=strided, n=n))
+    d.apply((), 1, 1, r3c_split_join, rows)         # join . join . map(map(row)) . split^rows
+    d.apply((), 2, 1, r4a_map, "map-workgroup")
+    R = ((2,), (0,))                                # the row: map(a) . reduce . map(mult) . zip(x)
+    if vw > 1:
+        d.apply(R, 2, 1, r4e_vectorize_map, vw)     # map(a) . R . asScalar . map(vect mult) . asVector . zip
+        d.apply(R, 1, 2, r3b_reorder)               # ... R . asScalar . reorder . map(vect) ...
+        d.apply(R, 1, 2, r3d_partial_vectors, J)    # map(a) . R . join . map(R . asScalar) . split^J . reorder . map(vect) . asVector . zip
+        d.apply(R, 5, 2, r3b_reorder_map)           # ... split^J . map(vect) . reorder . asVector . zip
+        d.apply(R, 4, 2, r3c_split_map)             # ... map(map(vect)) . split^J . reorder ...
+        d.apply(R, 3, 2, r3f_fuse_maps)             # map(a) . R . join . map(R . asScalar . map(vect)) . split^J ...
+        d.apply(R + ((3,),), 0, 3, r4e_lane_fold)   # work-item: reduce-seq(+) . asScalar . reduce-seq(vect(fold))
+    else:
+        d.apply(R, 1, 1, r3b_reorder)               # map(a) . R . reorder . map(mult) . zip
+        d.apply(R, 1, 1, r3d_partial, J)            # map(a) . R . join . map(R) . split^J . reorder . map(mult) . zip
+        d.apply(R, 5, 2, r3b_reorder_map)           # ... split^J . map(mult) . reorder . zip
+        d.apply(R, 4, 2, r3c_split_map)             # ... map(map(mult)) . split^J . reorder . zip
+        d.apply(R, 3, 2, r3f_fuse_maps)             # map(a) . R . join . map(R . map(mult)) . split^J . reorder . zip
+        d.apply(R + ((3,),), 0, 1, r4b_reduce)      # work-item: reduce-seq(+) . map(mult)
+        d.apply(R + ((3,),), 0, 2, r3f_fold)        # work-item: reduce-seq(fold(+, mult))
+    d.apply(R, 5, 1, r4c_reorder, 32 if strided else 0)
+    d.apply(R, 3, 1, r4a_map, "map-local")          # the 32 work-items of the row
+    d.apply(R, 1, 1, r3a_iterate, 5)                # the halving tree over their 32 sums
+    _lower_tree(d, R + ((1,),))
+    d.apply(R, 0, 1, r4a_map, "map-seq")            # a * (the row's dot)
+    return d
+
+
 def derive(op: str) -> Iterator[Derivation]:
     """Every derivation of an op over the parameter sets."""
     if op in REDUCTIONS:
@@ -506,6 +564,12 @@ def derive(op: str) -> Iterator[Derivation]:
         for tile, vw, t, staged in itertools.product(TILES, WIDTHS, WG_SIZES, (False, True)):
             try:
                 yield derive_map(op, tile, vw, t, staged)
+            except NotApplicable:
+                continue
+    elif op == "gemv":
+        for rows, vw, strided in itertools.product(GEMV_ROWS, WIDTHS, (True, False)):
+            try:
+                yield derive_gemv(rows, vw, strided)
             except NotApplicable:
                 continue
     else:
@@ -555,6 +619,25 @@ def parameters(e) -> Optional[Dict[str, Any]]:
             return None
         J = b[2].n
         return dict(kind="map", tile=fs[2].n, vw=vw, threads=fs[2].n // (vw * J), staged=staged)
+    # --- gemv: join . join . map-workgroup(map(ROW)) . split^rows, ROW =
+    # map-seq(a) . TREE32 . join . map-local(THREAD) . split^J
+    #   [. reorder-stride^32] [. asVector^vw] . zip(x)
+    if (len(fs) == 4 and isinstance(fs[0], Join) and isinstance(fs[1], Join)
+            and isinstance(fs[2], Map) and fs[2].kind == "map-workgroup"
+            and isinstance(fs[2].f, Map) and fs[2].f.kind == "map" and isinstance(fs[3], Split)):
+        r = list(parts(fs[2].f.f))
+        if not (r and isinstance(r[-1], ZipWith)):
+            return None
+        r = r[:-1]
+        vw = r.pop().n if isinstance(r[-1], AsVector) else 1
+        strided = isinstance(r[-1], ReorderStride)
+        if strided and r.pop().s != 32:
+            return None
+        if not (len(r) == 5 and isinstance(r[0], Map) and r[0].kind == "map-seq"
+                and _is_halving(r[1], 5) and isinstance(r[2], Join) and isinstance(r[3], Map)
+                and r[3].kind == "map-local" and isinstance(r[4], Split)):
+            return None
+        return dict(kind="gemv", rows=fs[3].n, vw=vw, lanes=32, strided=strided)
     # --- reductions
     if not (len(fs) == 4 and isinstance(fs[0], Reduce) and fs[0].kind == "reduce-seq"
             and isinstance(fs[1], Join) and isinstance(fs[2], Map)
@@ -597,7 +680,7 @@ def parameters(e) -> Optional[Dict[str, Any]]:
 # ---------------------------------------------------------------------------
 # the library's variants reached by derivations
 # ---------------------------------------------------------------------------
-OP_IDS = {"asum": 0, "dot": 1, "scal": 2, "nrm2": 8, "sum": 9, "axpy": 10}
+OP_IDS = {"asum": 0, "dot": 1, "scal": 2, "gemv": 3, "nrm2": 8, "sum": 9, "axpy": 10}
 
 
 def variant_key(info: Dict[str, Any]) -> Optional[Tuple]:
@@ -607,6 +690,13 @@ def variant_key(info: Dict[str, Any]) -> Optional[Tuple]:
         return None
     if info["op"] in (OP_IDS["scal"], OP_IDS["axpy"]):
         return ("map", info["tile"], info["vw"], info["threads"], info["stages"] > 0)
+    if info["op"] == OP_IDS["gemv"]:
+        # the warp-per-row family; the staged, tensor-copy and split-row
+        # forms move rows through shared memory or across CTAs in ways the
+        # enumerated gemv derivation does not take
+        if info["lanes"] == 32 and info["stages"] == 0 and info["tree"] == 0:
+            return ("gemv", info["rows"], info["vw"], bool(info["stride"]))
+        return None
     tree = {0: "warp", 1: "two"}.get(info["tree"])
     return ("reduce", info["tile"], info["vw"], info["threads"], bool(info["stride"]), tree,
             info["stages"] > 0)
@@ -615,6 +705,8 @@ def variant_key(info: Dict[str, Any]) -> Optional[Tuple]:
 def param_key(p: Dict[str, Any]) -> Tuple:
     if p["kind"] == "map":
         return ("map", p["tile"], p["vw"], p["threads"], p["staged"])
+    if p["kind"] == "gemv":
+        return ("gemv", p["rows"], p["vw"], p["strided"])
     return ("reduce", p["tile"], p["vw"], p["threads"], p["strided"], p["tree"], p["staged"])
 
 

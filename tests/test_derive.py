@@ -53,6 +53,8 @@ def to_oracle(e):
         return P.ToLocal(to_oracle(e.f))
     if isinstance(e, D.Pad):
         return P.PadTo(e.n)
+    if isinstance(e, D.ZipWith):
+        return P.ZipWith(e.name)
     raise TypeError(e)
 
 
@@ -94,6 +96,41 @@ def test_every_map_derivation_computes_the_program():
         assert np.array_equal(np.asarray(got), 3.0 * x), d.choice
 
 
+GEMV_Z = P.C(P.Join(), P.Map(P.C(P.Map(P.mult_by(3.0)), P.Reduce(P.add, 0), P.Map(P.mult),
+                                 P.ZipWith("x"))))
+
+
+def test_every_gemv_derivation_computes_the_program():
+    """Fig. 5's gemv z = join . map(scal(a) . dot(x)) over the rows of A: each
+    derivation (rows per work-group, vector width, strided or contiguous
+    work-item order) evaluates to the program exactly on integer inputs."""
+    ders = list(D.derive("gemv"))
+    assert len(ders) == len(D.GEMV_ROWS) * len(D.WIDTHS) * 2
+    for d in ders:
+        rng = np.random.default_rng(d.choice["rows"] * 10 + d.choice["vw"])
+        M, N = 2 * d.choice["rows"], d.choice["n"]
+        A = rng.integers(-20, 20, (M, N)).astype(float)
+        x = rng.integers(-20, 20, N).astype(float)
+        got = P.evaluate(to_oracle(d.expr), A, env={"x": x})
+        want = P.evaluate(GEMV_Z, A, env={"x": x})
+        assert np.array_equal(np.asarray(got), np.asarray(want)), d.choice
+        assert np.array_equal(np.asarray(want), 3.0 * (A @ x))
+
+
+def test_gemv_parameters_read_back_the_choices():
+    for d in D.derive("gemv"):
+        p = D.parameters(d.expr)
+        assert p == dict(kind="gemv", rows=d.choice["rows"], vw=d.choice["vw"], lanes=32,
+                         strided=d.choice["strided"]), (d.choice, p)
+    # a tree that is not the 32-lane halving tree has no template
+    d = D.derive_gemv(8, 4, True)
+    row = list(D.parts(d.expr.fs[2].f.f))
+    row[1] = D.Iterate(4, row[1].f)
+    bad = D.comp(*(list(d.expr.fs[:2]) + [D.Map("map-workgroup", D.Map("map", D.comp(*row)))]
+                   + [d.expr.fs[3]]))
+    assert D.parameters(bad) is None
+
+
 def test_parameters_read_back_the_choices():
     seen_rejected = 0
     for op in ("asum", "dot", "scal"):
@@ -130,6 +167,11 @@ def test_library_variants_reached_and_not():
     assert "asum_t4096_v4_tma4_p1" in r["library_reached"]        # toLocal staging (4d)
     assert all("_c" in n for n in r["library_not_derivable"])   # only cluster stages
     assert len(D.derivable_variants("scal")) == lift.lift_variant_count(lift.OP_SCAL)
+    # gemv: the warp-per-row family (persistent and one CTA per row group)
+    # and nothing else
+    warp = [v for v in range(lift.lift_variant_count(lift.OP_GEMV))
+            if lift.lift_variant_describe(lift.OP_GEMV, v)["name"].startswith("gemv_w")]
+    assert D.derivable_variants("gemv") == warp and len(warp) == 13
     derived = [n for n in r["library_reached"] if n.startswith("asum_d")]
     assert len(derived) == sum(ln.startswith("LIFT_DERIVED(0,") for ln in D.emit_lines())
 
