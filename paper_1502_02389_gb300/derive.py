@@ -510,18 +510,23 @@ def derive_map(op: str, tile: int, vw: int, threads: int, staged: bool) -> Deriv
     return d
 
 
-def derive_gemv(rows: int, vw: int, strided: bool, n: int = GEMV_N) -> Derivation:
+def derive_gemv(rows: int, vw: int, strided: bool, staged: bool = False,
+                n: int = GEMV_N) -> Derivation:
     """One derivation of gemv's z (Fig. 5) for rows of n elements, the form of
     the warp-per-row kernels: the rows split into work-groups of `rows`,
     each row's dot done by 32 work-items (a warp; like the 32-groups of a
     two-level reduction tree, the map over a work-group's rows stays a
     plain map) that each fold J = n / (32 vw) vectors of the row zipped with
     x (taken strided or as a contiguous run), then a halving tree over the
-    32 partial sums, then the scaling by a."""
+    32 partial sums, then the scaling by a.  Staged: the zipped row (A's row
+    and x) is copied to local memory first (Fig. 4d), the form of the
+    bulk-copy and tensor-copy kernels, which stream it through a ring of
+    shared-memory stages."""
     J = n // (32 * vw)
     if J < 1 or J * 32 * vw != n:
         raise NotApplicable
-    d = Derivation("gemv", program("gemv"), choice=dict(rows=rows, vw=vw, strided=strided, n=n))
+    d = Derivation("gemv", program("gemv"),
+                   choice=dict(rows=rows, vw=vw, strided=strided, staged=staged, n=n))
     d.apply((), 1, 1, r3c_split_join, rows)         # join . join . map(map(row)) . split^rows
     d.apply((), 2, 1, r4a_map, "map-workgroup")
     R = ((2,), (0,))                                # the row: map(a) . reduce . map(mult) . zip(x)
@@ -546,6 +551,9 @@ def derive_gemv(rows: int, vw: int, strided: bool, n: int = GEMV_N) -> Derivatio
     d.apply(R, 1, 1, r3a_iterate, 5)                # the halving tree over their 32 sums
     _lower_tree(d, R + ((1,),))
     d.apply(R, 0, 1, r4a_map, "map-seq")            # a * (the row's dot)
+    if staged:                                      # ... . toLocal(map-local(id)) . zip(x)
+        n_row = len(parts(_body(parts(_body(parts(d.expr)[2]))[0])))
+        d.apply(R, n_row - 2, 1, r4d_to_local)
     return d
 
 
@@ -567,9 +575,10 @@ def derive(op: str) -> Iterator[Derivation]:
             except NotApplicable:
                 continue
     elif op == "gemv":
-        for rows, vw, strided in itertools.product(GEMV_ROWS, WIDTHS, (True, False)):
+        for rows, vw, strided, staged in itertools.product(GEMV_ROWS, WIDTHS, (True, False),
+                                                            (False, True)):
             try:
-                yield derive_gemv(rows, vw, strided)
+                yield derive_gemv(rows, vw, strided, staged)
             except NotApplicable:
                 continue
     else:
@@ -629,6 +638,9 @@ def parameters(e) -> Optional[Dict[str, Any]]:
         if not (r and isinstance(r[-1], ZipWith)):
             return None
         r = r[:-1]
+        staged = isinstance(r[-1], ToLocal)
+        if staged:
+            r = r[:-1]
         vw = r.pop().n if isinstance(r[-1], AsVector) else 1
         strided = isinstance(r[-1], ReorderStride)
         if strided and r.pop().s != 32:
@@ -637,7 +649,7 @@ def parameters(e) -> Optional[Dict[str, Any]]:
                 and _is_halving(r[1], 5) and isinstance(r[2], Join) and isinstance(r[3], Map)
                 and r[3].kind == "map-local" and isinstance(r[4], Split)):
             return None
-        return dict(kind="gemv", rows=fs[3].n, vw=vw, lanes=32, strided=strided)
+        return dict(kind="gemv", rows=fs[3].n, vw=vw, lanes=32, strided=strided, staged=staged)
     # --- reductions
     if not (len(fs) == 4 and isinstance(fs[0], Reduce) and fs[0].kind == "reduce-seq"
             and isinstance(fs[1], Join) and isinstance(fs[2], Map)
@@ -691,11 +703,11 @@ def variant_key(info: Dict[str, Any]) -> Optional[Tuple]:
     if info["op"] in (OP_IDS["scal"], OP_IDS["axpy"]):
         return ("map", info["tile"], info["vw"], info["threads"], info["stages"] > 0)
     if info["op"] == OP_IDS["gemv"]:
-        # the warp-per-row family; the staged, tensor-copy and split-row
-        # forms move rows through shared memory or across CTAs in ways the
-        # enumerated gemv derivation does not take
-        if info["lanes"] == 32 and info["stages"] == 0 and info["tree"] == 0:
-            return ("gemv", info["rows"], info["vw"], bool(info["stride"]))
+        # a warp per row, direct or staged through shared memory (bulk or
+        # tensor copies: info tree 3); the split-row form, which spreads a
+        # row over several CTAs, is not among the enumerated derivations
+        if info["lanes"] == 32 and info["tree"] in (0, 3):
+            return ("gemv", info["rows"], info["vw"], bool(info["stride"]), info["stages"] > 0)
         return None
     tree = {0: "warp", 1: "two"}.get(info["tree"])
     return ("reduce", info["tile"], info["vw"], info["threads"], bool(info["stride"]), tree,
@@ -706,7 +718,7 @@ def param_key(p: Dict[str, Any]) -> Tuple:
     if p["kind"] == "map":
         return ("map", p["tile"], p["vw"], p["threads"], p["staged"])
     if p["kind"] == "gemv":
-        return ("gemv", p["rows"], p["vw"], p["strided"])
+        return ("gemv", p["rows"], p["vw"], p["strided"], p["staged"])
     return ("reduce", p["tile"], p["vw"], p["threads"], p["strided"], p["tree"], p["staged"])
 
 

@@ -103,9 +103,10 @@ GEMV_Z = P.C(P.Join(), P.Map(P.C(P.Map(P.mult_by(3.0)), P.Reduce(P.add, 0), P.Ma
 def test_every_gemv_derivation_computes_the_program():
     """Fig. 5's gemv z = join . map(scal(a) . dot(x)) over the rows of A: each
     derivation (rows per work-group, vector width, strided or contiguous
-    work-item order) evaluates to the program exactly on integer inputs."""
+    work-item order, staged or not) evaluates to the program exactly on
+    integer inputs."""
     ders = list(D.derive("gemv"))
-    assert len(ders) == len(D.GEMV_ROWS) * len(D.WIDTHS) * 2
+    assert len(ders) == len(D.GEMV_ROWS) * len(D.WIDTHS) * 2 * 2
     for d in ders:
         rng = np.random.default_rng(d.choice["rows"] * 10 + d.choice["vw"])
         M, N = 2 * d.choice["rows"], d.choice["n"]
@@ -121,7 +122,7 @@ def test_gemv_parameters_read_back_the_choices():
     for d in D.derive("gemv"):
         p = D.parameters(d.expr)
         assert p == dict(kind="gemv", rows=d.choice["rows"], vw=d.choice["vw"], lanes=32,
-                         strided=d.choice["strided"]), (d.choice, p)
+                         strided=d.choice["strided"], staged=d.choice["staged"]), (d.choice, p)
     # a tree that is not the 32-lane halving tree has no template
     d = D.derive_gemv(8, 4, True)
     row = list(D.parts(d.expr.fs[2].f.f))
@@ -167,11 +168,13 @@ def test_library_variants_reached_and_not():
     assert "asum_t4096_v4_tma4_p1" in r["library_reached"]        # toLocal staging (4d)
     assert all("_c" in n for n in r["library_not_derivable"])   # only cluster stages
     assert len(D.derivable_variants("scal")) == lift.lift_variant_count(lift.OP_SCAL)
-    # gemv: the warp-per-row family (persistent and one CTA per row group)
-    # and nothing else
-    warp = [v for v in range(lift.lift_variant_count(lift.OP_GEMV))
-            if lift.lift_variant_describe(lift.OP_GEMV, v)["name"].startswith("gemv_w")]
-    assert D.derivable_variants("gemv") == warp and len(warp) == 13
+    # gemv: a warp per row, direct (persistent or one CTA per row group) or
+    # staged through shared memory (bulk or tensor copies); not the
+    # split-row form
+    names = [lift.lift_variant_describe(lift.OP_GEMV, v)["name"]
+             for v in range(lift.lift_variant_count(lift.OP_GEMV))]
+    reached = [v for v, nm in enumerate(names) if not nm.startswith("gemv_split")]
+    assert D.derivable_variants("gemv") == reached and len(reached) == 28
     derived = [n for n in r["library_reached"] if n.startswith("asum_d")]
     assert len(derived) == sum(ln.startswith("LIFT_DERIVED(0,") for ln in D.emit_lines())
 
