@@ -423,6 +423,31 @@ def derive_reduction(op: str, tile: int, vw: int, threads: int, strided: bool, t
     d.apply((), 3, 2, r3c_split_map)                # R . join . map(R) . map(map(g)) . split
     d.apply((), 2, 2, r3f_fuse_maps)                # R . join . map(R . map(g)) . split
     W = ((2,),)                                     # inside the work-group's map
+    _lower_workgroup(d, W, vw, J, threads, strided, tree)
+    if staged:
+        n = len(parts(_at(d.expr, W)))
+        d.apply(W, n - 1, 1, r4d_to_local)
+    d.apply((), 2, 1, r4a_map, "map-workgroup")
+    d.apply((), 0, 1, r4b_reduce)                   # the outer reduce over the work-groups
+    if op == "nrm2":
+        d.expr = comp(Map("map-seq", SQRT), d.expr)
+        d.steps.append(("sqrt of the sum (program)", ()))
+    return d
+
+
+def _at(e, where):
+    """The composition reached by descending through ``where`` (as in
+    ``rewrite``)."""
+    for (i,) in where:
+        e = _body(parts(e)[i])
+    return e
+
+
+def _lower_workgroup(d: Derivation, W, vw: int, J: int, threads: int, strided: bool, tree: str):
+    """The work-group body at W, reduce . map(g) over its tile, lowered: the
+    tile vectorised (vw > 1), reordered and split among `threads`
+    work-items that fold J elements (vectors) each with g fused in, then the
+    work-group tree over their results."""
     if vw > 1:
         d.apply(W, 1, 1, r4e_vectorize_map, vw)     # R . asScalar . map(vect g) . asVector
         d.apply(W, 0, 2, r3b_reorder)               # R . asScalar . reorder . ...
@@ -440,7 +465,7 @@ def derive_reduction(op: str, tile: int, vw: int, threads: int, strided: bool, t
         d.apply(W + ((2,),), 0, 1, r4b_reduce)      # thread: reduce-seq(+) . map(g)
         d.apply(W + ((2,),), 0, 2, r3f_fold)        # thread: reduce-seq(fold(+, g))
     # the thread order: reorder -> reorder-stride^threads (strided) | id (contiguous runs)
-    body = parts(_body(parts(d.expr)[2]))
+    body = parts(_at(d.expr, W))
     ro = [i for i, f in enumerate(body) if isinstance(f, Reorder)][0]
     d.apply(W, ro, 1, r4c_reorder, threads if strided else 0)
     d.apply(W, 2, 1, r4a_map, "map-local")          # threads
@@ -464,15 +489,6 @@ def derive_reduction(op: str, tile: int, vw: int, threads: int, strided: bool, t
         _lower_tree(d, W + ((0,),))
     else:
         raise NotApplicable
-    if staged:
-        n = len(parts(_body(parts(d.expr)[2])))
-        d.apply(W, n - 1, 1, r4d_to_local)
-    d.apply((), 2, 1, r4a_map, "map-workgroup")
-    d.apply((), 0, 1, r4b_reduce)                   # the outer reduce over the work-groups
-    if op == "nrm2":
-        d.expr = comp(Map("map-seq", SQRT), d.expr)
-        d.steps.append(("sqrt of the sum (program)", ()))
-    return d
 
 
 def _lower_tree(d: Derivation, it_where):
@@ -557,6 +573,40 @@ def derive_gemv(rows: int, vw: int, strided: bool, staged: bool = False,
     return d
 
 
+GEMV_SPLIT_N = 8192          # the row length the split-row derivations are written for
+GEMV_SEGMENTS = (1024, 2048, 4096)
+
+
+def derive_gemv_split(threads: int, vw: int, strided: bool, seg: int,
+                      n: int = GEMV_SPLIT_N) -> Derivation:
+    """One derivation of gemv's z with each row's reduce split by Fig. 3d into
+    S = n / seg segments of seg elements, one work-group per segment lowered
+    like a reduction's work-group (threads work-items folding strided or
+    contiguous vectors, the two-level tree), then the combine of the S
+    partials, padded to 32, by a halving tree (the warp of the second
+    launch: its own work-group, so the map of that tree stays a plain map),
+    then the scaling by a.  The rows stay a plain map (the grid's second
+    dimension)."""
+    J = seg // (vw * threads)
+    S = n // seg
+    if J < 1 or J * vw * threads != seg or S * seg != n or S > 32 or threads <= 32:
+        raise NotApplicable
+    d = Derivation("gemv", program("gemv"),
+                   choice=dict(split=True, threads=threads, vw=vw, strided=strided, seg=seg, n=n))
+    R = ((1,),)                                     # the row: map(a) . reduce . map(mult) . zip(x)
+    d.apply(R, 1, 1, r3d_partial, seg)              # map(a) . R . join . map(R) . split^seg . map(mult) . zip
+    d.apply(R, 4, 2, r3c_split_map)                 # ... map(R) . map(map(mult)) . split^seg . zip
+    d.apply(R, 3, 2, r3f_fuse_maps)                 # map(a) . R . join . map(R . map(mult)) . split^seg . zip
+    _lower_workgroup(d, R + ((3,),), vw, J, threads, strided, "two")
+    d.apply(R, 3, 1, r4a_map, "map-workgroup")      # a work-group per segment
+    d.apply(R, 1, 1, r_pad, 32)                     # the S partials padded to 32
+    d.apply(R, 1, 1, r3a_iterate, 5)                # the combine's halving tree
+    d.apply(R + ((1,), (1,)), 0, 1, r4b_reduce)
+    d.apply(R + ((1,),), 3, 1, r4c_reorder, 0, 2)
+    d.apply(R, 0, 1, r4a_map, "map-seq")            # a * (the row's dot)
+    return d
+
+
 def derive(op: str) -> Iterator[Derivation]:
     """Every derivation of an op over the parameter sets."""
     if op in REDUCTIONS:
@@ -581,6 +631,12 @@ def derive(op: str) -> Iterator[Derivation]:
                 yield derive_gemv(rows, vw, strided, staged)
             except NotApplicable:
                 continue
+        for threads, vw, strided, seg in itertools.product(WG_SIZES, WIDTHS, (True, False),
+                                                            GEMV_SEGMENTS):
+            try:
+                yield derive_gemv_split(threads, vw, strided, seg)
+            except NotApplicable:
+                continue
     else:
         raise KeyError(op)
 
@@ -588,12 +644,12 @@ def derive(op: str) -> Iterator[Derivation]:
 # ---------------------------------------------------------------------------
 # reading kernel parameters off a low-level expression
 # ---------------------------------------------------------------------------
-def _is_halving(e, levels: int) -> bool:
+def _is_halving(e, levels: int, kind: str = "map-local") -> bool:
     if not (isinstance(e, Iterate) and e.k == levels):
         return False
     b = parts(e.f)
     return (len(b) == 4 and isinstance(b[0], Join) and isinstance(b[1], Map)
-            and b[1].kind == "map-local" and isinstance(b[1].f, Reduce)
+            and b[1].kind == kind and isinstance(b[1].f, Reduce)
             and b[1].f.kind == "reduce-seq" and b[1].f.f == ADD and isinstance(b[2], Split)
             and b[2].n == 2 and b[3] == ReorderStride(0, 2))
 
@@ -650,13 +706,35 @@ def parameters(e) -> Optional[Dict[str, Any]]:
                 and r[3].kind == "map-local" and isinstance(r[4], Split)):
             return None
         return dict(kind="gemv", rows=fs[3].n, vw=vw, lanes=32, strided=strided, staged=staged)
+    # --- gemv with split rows: join . map(ROW), ROW = map-seq(a) . COMBINE
+    # . pad-32 . join . map-workgroup(SEGMENT) . split^L . zip(x), COMBINE a
+    # halving tree over 32 (the second launch's warp), SEGMENT a reduction
+    # work-group body
+    if (len(fs) == 2 and isinstance(fs[0], Join) and isinstance(fs[1], Map)
+            and fs[1].kind == "map"):
+        r = list(parts(fs[1].f))
+        if not (len(r) == 7 and isinstance(r[0], Map) and r[0].kind == "map-seq"
+                and _is_halving(r[1], 5, "map") and r[2] == Pad(32) and isinstance(r[3], Join)
+                and isinstance(r[4], Map) and r[4].kind == "map-workgroup"
+                and isinstance(r[5], Split) and isinstance(r[6], ZipWith)):
+            return None
+        w = _workgroup_params(list(parts(r[4].f)), r[5].n)
+        if w is None or w["tree"] != "two" or w["staged"]:
+            return None
+        return dict(kind="gemv_split", threads=w["threads"], vw=w["vw"], strided=w["strided"])
     # --- reductions
     if not (len(fs) == 4 and isinstance(fs[0], Reduce) and fs[0].kind == "reduce-seq"
             and isinstance(fs[1], Join) and isinstance(fs[2], Map)
             and fs[2].kind == "map-workgroup" and isinstance(fs[3], Split)):
         return None
-    tile = fs[3].n
-    b = list(parts(fs[2].f))
+    w = _workgroup_params(list(parts(fs[2].f)), fs[3].n)
+    return None if w is None else dict(kind="reduce", **w)
+
+
+def _workgroup_params(b, tile: int) -> Optional[Dict[str, Any]]:
+    """(tile, vw, threads, strided, tree, staged) of a reduction's work-group
+    body TREE . join . map-local(THREAD) . split^J [. reorder-stride^T]
+    [. asVector^vw] [. toLocal(map-local(id))] over `tile` elements."""
     staged = isinstance(b[-1], ToLocal)
     if staged:
         b = b[:-1]
@@ -685,8 +763,7 @@ def parameters(e) -> Optional[Dict[str, Any]]:
         form = "two"
     else:
         return None        # e.g. one halving tree over more than 32 work-items
-    return dict(kind="reduce", tile=tile, vw=vw, threads=threads, strided=strided, tree=form,
-                staged=staged)
+    return dict(tile=tile, vw=vw, threads=threads, strided=strided, tree=form, staged=staged)
 
 
 # ---------------------------------------------------------------------------
@@ -708,6 +785,8 @@ def variant_key(info: Dict[str, Any]) -> Optional[Tuple]:
         # row over several CTAs, is not among the enumerated derivations
         if info["lanes"] == 32 and info["tree"] in (0, 3):
             return ("gemv", info["rows"], info["vw"], bool(info["stride"]), info["stages"] > 0)
+        if info["lanes"] == info["threads"] > 32 and info["rows"] == 1:     # rows split over CTAs
+            return ("gemv_split", info["threads"], info["vw"], bool(info["stride"]))
         return None
     tree = {0: "warp", 1: "two"}.get(info["tree"])
     return ("reduce", info["tile"], info["vw"], info["threads"], bool(info["stride"]), tree,
@@ -719,6 +798,8 @@ def param_key(p: Dict[str, Any]) -> Tuple:
         return ("map", p["tile"], p["vw"], p["threads"], p["staged"])
     if p["kind"] == "gemv":
         return ("gemv", p["rows"], p["vw"], p["strided"], p["staged"])
+    if p["kind"] == "gemv_split":
+        return ("gemv_split", p["threads"], p["vw"], p["strided"])
     return ("reduce", p["tile"], p["vw"], p["threads"], p["strided"], p["tree"], p["staged"])
 
 

@@ -102,14 +102,17 @@ GEMV_Z = P.C(P.Join(), P.Map(P.C(P.Map(P.mult_by(3.0)), P.Reduce(P.add, 0), P.Ma
 
 def test_every_gemv_derivation_computes_the_program():
     """Fig. 5's gemv z = join . map(scal(a) . dot(x)) over the rows of A: each
-    derivation (rows per work-group, vector width, strided or contiguous
-    work-item order, staged or not) evaluates to the program exactly on
-    integer inputs."""
+    derivation -- a warp per row (rows per work-group, vector width, strided
+    or contiguous work-item order, staged or not) or each row split over
+    work-groups (work-items, vector width, order, segment length) --
+    evaluates to the program exactly on integer inputs."""
     ders = list(D.derive("gemv"))
-    assert len(ders) == len(D.GEMV_ROWS) * len(D.WIDTHS) * 2 * 2
-    for d in ders:
-        rng = np.random.default_rng(d.choice["rows"] * 10 + d.choice["vw"])
-        M, N = 2 * d.choice["rows"], d.choice["n"]
+    warp = [d for d in ders if not d.choice.get("split")]
+    split = [d for d in ders if d.choice.get("split")]
+    assert len(warp) == len(D.GEMV_ROWS) * len(D.WIDTHS) * 2 * 2 and len(split) > 50
+    rng = np.random.default_rng(4)
+    for d in warp + [split[i] for i in rng.choice(len(split), 20, replace=False)]:
+        M, N = 2 * d.choice.get("rows", 1), d.choice["n"]
         A = rng.integers(-20, 20, (M, N)).astype(float)
         x = rng.integers(-20, 20, N).astype(float)
         got = P.evaluate(to_oracle(d.expr), A, env={"x": x})
@@ -121,8 +124,13 @@ def test_every_gemv_derivation_computes_the_program():
 def test_gemv_parameters_read_back_the_choices():
     for d in D.derive("gemv"):
         p = D.parameters(d.expr)
-        assert p == dict(kind="gemv", rows=d.choice["rows"], vw=d.choice["vw"], lanes=32,
-                         strided=d.choice["strided"], staged=d.choice["staged"]), (d.choice, p)
+        c = d.choice
+        if c.get("split"):
+            assert p == dict(kind="gemv_split", threads=c["threads"], vw=c["vw"],
+                             strided=c["strided"]), (c, p)
+        else:
+            assert p == dict(kind="gemv", rows=c["rows"], vw=c["vw"], lanes=32,
+                             strided=c["strided"], staged=c["staged"]), (c, p)
     # a tree that is not the 32-lane halving tree has no template
     d = D.derive_gemv(8, 4, True)
     row = list(D.parts(d.expr.fs[2].f.f))
@@ -168,13 +176,10 @@ def test_library_variants_reached_and_not():
     assert "asum_t4096_v4_tma4_p1" in r["library_reached"]        # toLocal staging (4d)
     assert all("_c" in n for n in r["library_not_derivable"])   # only cluster stages
     assert len(D.derivable_variants("scal")) == lift.lift_variant_count(lift.OP_SCAL)
-    # gemv: a warp per row, direct (persistent or one CTA per row group) or
-    # staged through shared memory (bulk or tensor copies); not the
-    # split-row form
-    names = [lift.lift_variant_describe(lift.OP_GEMV, v)["name"]
-             for v in range(lift.lift_variant_count(lift.OP_GEMV))]
-    reached = [v for v, nm in enumerate(names) if not nm.startswith("gemv_split")]
-    assert D.derivable_variants("gemv") == reached and len(reached) == 28
+    # gemv: every variant -- a warp per row, direct (persistent or one CTA
+    # per row group) or staged through shared memory (bulk or tensor
+    # copies), and the rows split over CTAs
+    assert D.derivable_variants("gemv") == list(range(lift.lift_variant_count(lift.OP_GEMV)))
     derived = [n for n in r["library_reached"] if n.startswith("asum_d")]
     assert len(derived) == sum(ln.startswith("LIFT_DERIVED(0,") for ln in D.emit_lines())
 
