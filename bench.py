@@ -12,14 +12,19 @@ its fraction of the measured HBM peak.  Inputs (3 x 256 MiB) exceed the
 129 MB L2, so no flush is needed between steps.
 
 Other workloads (``--workload``): asum (n = 2^20, L2 flushed before every
-step), gemv_square (8192 x 8192), gemv_tall (65536 x 1024).
+step), gemv_square (8192 x 8192), gemv_tall (65536 x 1024), mixed (bf16 and
+fp8 asum / dot at 2^28), batch (20,000 ops), and more.  A default run (the
+dot/scal workload on one GPU) also measures asum, both gemv shapes, mixed
+and batch after the headline step, each with its own roofline, oracle check
+and CPU baseline, under ``config.sub`` (``--no-sub`` skips them).
 
 Under torchrun each rank runs its own replica on its own GPU (the ops of
 one step do not exchange data); value is the bytes of all ranks divided by
 the slowest rank's time.
 
 ``--impl reference`` times the CPU oracle instead (the FP64 pattern
-interpreter on the host cores) on a bounded sample of the same workload.
+interpreter on one host core): W warm-up and exactly K timed steps, each one
+call of the oracle on the workload or its stated bounded slice.
 """
 from __future__ import annotations
 
@@ -334,25 +339,21 @@ def run_ours(args, rank, world, dist):
                     ev3.record(s)
                     kscal[2].append(ev2); kscal[3].append(ev3)
 
-        # end to end: the step pipelined over E2E_CHUNKS slices of whole tiles,
-        # host->device copies, the batched dot + scal of a slice, and the
-        # device->host copy of its scal output on three streams, so the two
-        # copy directions and the kernels overlap; the dot is the FP64 sum of
-        # the slices' partial dots, read back with the last slice
+        # end to end: the step pipelined over E2E_CHUNKS slices of whole tiles
+        # on three streams (host->device copies; the slice's dot partial and
+        # scal; the device->host copy of its scal output), so the two copy
+        # directions and the kernels overlap.  Each slice's dot goes to one
+        # FP64 partial on the device (lift_dot_partial); after the last slice
+        # the partials come back and lift_combine_partials adds them in slice
+        # order and rounds once: the step returns the dot of the whole vectors.
         C = E2E_CHUNKS
         chunk = n // C
-        rparts = torch.zeros(C, device=dev)
-        hbc = [batch_create(args, [
-            {"op": lift.OP_DOT, "variant": vd, "n": chunk, "x": x[c * chunk:(c + 1) * chunk],
-             "y": y[c * chunk:(c + 1) * chunk], "out": rparts[c:c + 1]},
-            {"op": lift.OP_SCAL, "variant": vs, "n": chunk, "alpha": float(alpha),
-             "x": x[c * chunk:(c + 1) * chunk], "out": z[c * chunk:(c + 1) * chunk]}])
-            for c in range(C)]
+        parts64 = torch.zeros(C, dtype=torch.float64, device=dev)
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
         ev_in = [torch.cuda.Event() for _ in range(C)]
         ev_done = [torch.cuda.Event() for _ in range(C)]
 
-        def e2e_step(xp, yp, zp, rp):
+        def e2e_step(xp, yp, zp, pp):
             s_in.wait_stream(s)
             for c in range(C):
                 sl = slice(c * chunk, (c + 1) * chunk)
@@ -361,20 +362,23 @@ def run_ours(args, rank, world, dist):
                     y[sl].copy_(yp[sl], non_blocking=True)
                 ev_in[c].record(s_in)
                 s.wait_event(ev_in[c])
-                lift.lift_batch_run(hbc[c], s)
+                lift.lift_dot_partial(x[sl], y[sl], chunk, parts64[c:c + 1], s)
+                lift.lift_scal_v(vs, chunk, float(alpha), x[sl], z[sl], s)
                 ev_done[c].record(s)
                 s_out.wait_event(ev_done[c])
                 with torch.cuda.stream(s_out):
                     zp[sl].copy_(z[sl], non_blocking=True)
             with torch.cuda.stream(s_out):
-                rp.copy_(rparts, non_blocking=True)
+                pp.copy_(parts64, non_blocking=True)
             s.wait_stream(s_out)
+            s_out.synchronize()
+            return lift.lift_combine_partials(pp.tolist())[0]
 
         host = dict(xp=torch.from_numpy(xh).pin_memory(), yp=torch.from_numpy(yh).pin_memory(),
                     zp=torch.empty(n, dtype=torch.float32).pin_memory(),
-                    rp=torch.empty(C, dtype=torch.float32).pin_memory())
+                    pp=torch.empty(C, dtype=torch.float64).pin_memory())
         collect = lambda: {"dot": float(r.item()), "scal": z.cpu().numpy()}  # noqa: E731
-        h2d, d2h = 8 * n, 4 * n + 4 * C
+        h2d, d2h = 8 * n, 4 * n + 8 * C
         config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pd["name"], ps["name"]],
                   "submitted_as": ("one batched launch of the two calls (lift_batch_run)"
                                    if args.mode == "batched" else
@@ -553,17 +557,20 @@ def run_ours(args, rank, world, dist):
             descs.append(q)
         policies = {"fixed": (lift.POLICY_FIXED, None)}
         table = os.path.join(tempfile.gettempdir(), f"lift_bench_table_{os.getpid()}.txt")
-        try:
-            from paper_1502_02389_gb300 import tune
-            recs = tune.load_csv(os.path.join(costmodel.DATA, "timings_gb300_train.csv"))
-            os.makedirs(os.path.dirname(table), exist_ok=True)
-            tune.write_table(recs, table)
-            policies["table"] = (lift.POLICY_TABLE, table)
-        except (OSError, AssertionError):
-            pass
+        if not args.no_extras:          # the other policies, for comparison
+            try:
+                from paper_1502_02389_gb300 import tune
+                recs = tune.load_csv(os.path.join(costmodel.DATA, "timings_gb300_train.csv"))
+                os.makedirs(os.path.dirname(table), exist_ok=True)
+                tune.write_table(recs, table)
+                policies["table"] = (lift.POLICY_TABLE, table)
+            except (OSError, AssertionError):
+                pass
         weights = args.mlp or costmodel.WEIGHTS
         if os.path.exists(weights):
             policies["mlp"] = (lift.POLICY_MLP, weights)
+            if args.no_extras:
+                del policies["fixed"]
         handles = {}
         for name, (pol, path) in policies.items():
             lift.lift_set_policy(pol, path)
@@ -600,6 +607,32 @@ def run_ours(args, rank, world, dist):
                 torch.cuda.synchronize()
                 out[name] = round(bytes_step * 5 / (a.elapsed_time(b) / 1e3) / 1e9, 1)
             return out
+
+        # the oracle check: a fixed sample of ops; the sampled gemv outputs
+        # (updated in place by every run) are put back to their initial
+        # values and the batch run once more before they are read
+        chk = np.sort(np.random.default_rng(7).choice(len(ops), min(200, len(ops)), replace=False))
+        y0 = {int(i): pool[lay[i]["out"]:lay[i]["out"] + ops[i]["M"]].clone()
+              for i in chk if ops[i]["op"] == synth.GEMV}
+
+        def collect():
+            for i, t in y0.items():
+                pool[lay[i]["out"]:lay[i]["out"] + ops[i]["M"]].copy_(t)
+            lift.lift_batch_run(hb)
+            torch.cuda.synchronize()
+            out = []
+            for i in chk:
+                d, e = ops[int(i)], lay[int(i)]
+                get = lambda k, c: pool[e[k]:e[k] + c].cpu().numpy()  # noqa: E731
+                if d["op"] == synth.GEMV:
+                    out.append((d, {"A": get("A", d["M"] * d["N"]).reshape(d["M"], d["N"]),
+                                    "x": get("x", d["N"]), "y0": y0[int(i)].cpu().numpy(),
+                                    "got": get("out", d["M"])}))
+                else:
+                    out.append((d, {"x": get("x", d["n"]),
+                                    "y": get("y", d["n"]) if d["op"] == synth.DOT else None,
+                                    "got": float(pool[e["out"]].item())}))
+            return {"ops": out, "of": len(ops)}
 
         e2e_step, host, h2d, d2h = None, {}, 0, 0
         config = {"workload": WORKLOADS[wl]["desc"], "ops": len(ops), "items": info["items"],
@@ -696,27 +729,30 @@ def run_ours(args, rank, world, dist):
             "algorithmic_bytes_per_launch": kernels[[k[0] for k in kernels].index(dom)][1]}
 
     # ---- end to end through the C-ABI with host buffers
+    # (host clock around the steps, synchronised on both sides: the region
+    # holds the copies, the kernels and any host-side finishing of a result)
     e2e = None
-    if e2e_step is not None:
+    if e2e_step is not None and not args.no_e2e:
         for _ in range(2):
             e2e_step(**host)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ek = max(3, min(args.steps, 10))
-        e0.record(s)
+        t_e = time.perf_counter()
         for _ in range(ek):
-            e2e_step(**host)
-        e1.record(s)
+            e2e_result = e2e_step(**host)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / ek
+        ems = (time.perf_counter() - t_e) * 1e3 / ek
         ems = max_over_ranks(ems, dist, dev)
         e2e = {"value": round(world * bytes_step / (ems / 1e3) / 1e9, 2), "unit": "GB/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4)}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 4),
+               "timer": "host clock, synchronised on both sides"}
+        if e2e_result is not None:
+            e2e["result"] = e2e_result
     if e2e is not None and wl in ("dot_scal", "blackscholes"):
         e2e["pipelined"] = f"{E2E_CHUNKS} slices; H2D, kernels and D2H on three streams"
     if e2e is not None and wl == "dot_scal":
-        for h in hbc:
-            lift.lift_batch_destroy(h)
+        e2e["result_formed"] = ("dot of the whole vectors: FP64 slice partials "
+                                "(lift_dot_partial) added by lift_combine_partials")
     if wl == "dot_scal" and args.no_extras:
         lift.lift_batch_destroy(hb2)
     elif wl == "dot_scal":
@@ -743,6 +779,8 @@ def run_ours(args, rank, world, dist):
             lift.lift_batch_destroy(h)
     assert lift.lift_read_status() == 0
     results = collect() if (collect is not None and rank == 0) else None
+    if results is not None and e2e is not None and "result" in e2e:
+        results["e2e_dot"] = e2e["result"]
     torch.cuda.synchronize()
     return dict(value=value, ms_step=ms_step, roofline=roof, per_kernel=per_kernel, clocks=clk,
                 results=results,
@@ -752,10 +790,10 @@ def run_ours(args, rank, world, dist):
 # ---------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(workload: str, budget_s: float):
-    """Time the oracle, as it stands, on the workload (or a bounded slice of
-    it) until about ``budget_s`` seconds of CPU work; returns GB/s of
-    algorithmic bytes and a description of the sample."""
+def oracle_work(workload: str):
+    """One step of the oracle, as it stands, on the workload or a bounded
+    slice of it: (work, algorithmic bytes of one call of work, description
+    of the sample)."""
     import numpy as np
 
     from oracle import blas
@@ -830,6 +868,14 @@ def oracle_sample(workload: str, budget_s: float):
         As, ys = A[:rows], yv[:rows]
         work = lambda: blas.gemv(As, xv, ys, float(a), float(b))  # noqa: E731
         bytes_one, what = 4 * rows * N + 4 * N + 8 * rows, f"first {rows} of {M} rows"
+    return work, bytes_one, what
+
+
+def oracle_sample(workload: str, budget_s: float):
+    """Time the oracle, as it stands, on the workload (or a bounded slice of
+    it) until about ``budget_s`` seconds of CPU work; returns GB/s of
+    algorithmic bytes and a description of the sample."""
+    work, bytes_one, what = oracle_work(workload)
     reps, t0 = 0, time.perf_counter()
     while True:
         work()
@@ -933,7 +979,10 @@ def oracle_accuracy(workload: str, results):
     if workload == "dot_scal":
         n = WORKLOADS[workload]["n"]
         x, y, alpha = synth.dot_scal(n)
-        out["dot"] = entry(results["dot"], blas.dot(x, y), blas.tolerance(n, blas.dot_terms(x, y)))
+        ref, tol = blas.dot(x, y), blas.tolerance(n, blas.dot_terms(x, y))
+        out["dot"] = entry(results["dot"], ref, tol)
+        if results.get("e2e_dot") is not None:
+            out["e2e_dot"] = entry(results["e2e_dot"], ref, tol)
         want = (np.float64(alpha) * x.astype(np.float64)).astype(np.float32)
         out["scal"] = {"bit_exact": bool(np.array_equal(results["scal"], want)), "elements": n}
     elif workload in ("asum", "asum_large"):
@@ -968,6 +1017,27 @@ def oracle_accuracy(workload: str, results):
             ratio = np.abs(got.astype(np.float64) - ref) / tol
             out[name] = {"max_abs_err": float(np.max(np.abs(got - ref))), "max_ratio": float(np.max(ratio)),
                          "options": m}
+    elif workload == "batch":
+        worst, count = 0.0, 0
+        for d, a in results["ops"]:
+            if d["op"] == synth.GEMV:
+                A, x, y0 = (a[k].astype(np.float64) for k in ("A", "x", "y0"))
+                ref = blas.gemv(A, x, y0, 1.0, 0.5)
+                tol = blas.tolerance(d["N"], 1.0) * blas.gemv_row_terms(a["A"], a["x"], a["y0"], 1.0, 0.5)
+                r = np.abs(a["got"].astype(np.float64) - ref) / tol
+                worst = max(worst, float(np.max(r)) if r.size else 0.0)
+            else:
+                x = a["x"].astype(np.float64)
+                if d["op"] == synth.ASUM:
+                    ref, terms = blas.asum(x), blas.asum_terms(x)
+                else:
+                    y = a["y"].astype(np.float64)
+                    ref, terms = blas.dot(x, y), blas.dot_terms(x, y)
+                tol = blas.tolerance(d["n"], terms)
+                worst = max(worst, abs(a["got"] - ref) / tol if tol > 0 else float(a["got"] != ref))
+            count += 1
+        out["ops"] = {"checked": count, "of": results["of"], "max_ratio": worst,
+                      "sample": "fixed random sample (seed 7); every op in the GPU tests"}
     elif workload in ("gemv_square", "gemv_tall", "gemv_t_square", "gemv_t_tall"):
         M, N = WORKLOADS[workload]["M"], WORKLOADS[workload]["N"]
         idx = results["index"]
@@ -992,9 +1062,21 @@ def oracle_accuracy(workload: str, results):
 
 
 def run_reference(args):
-    val, sample, sec = oracle_sample(args.workload, budget_s=max(3.0, 20.0 / max(1, args.steps)))
+    """The oracle as the reference arm: W untimed and exactly K timed steps,
+    each step one call of the oracle on the workload (or its stated bounded
+    slice), on one host core."""
+    work, bytes_one, what = oracle_work(args.workload)
+    for _ in range(args.warmup):
+        work()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        work()
+    el = time.perf_counter() - t0
+    val = bytes_one * args.steps / el / 1e9
+    sample = f"{what}; {args.steps} timed step(s) after {args.warmup} warm-up step(s), {el:.1f} s"
     out = {"metric": METRIC, "value": round(val, 4), "unit": "GB/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 2),
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(el / args.steps * 1e3, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOADS[args.workload]["desc"]},
@@ -1006,6 +1088,38 @@ def run_reference(args):
 
 
 METRIC = "HBM GB/s (frac of peak) for asum/dot/gemv; learned vs autotuned variant gap"
+
+# the other configurations of the metric, measured in the same run after the
+# headline step: asum at 2^20 (L2 flushed), both gemv shapes, the bf16 and fp8
+# ops at 2^28, and the 20,000-op batched launch
+SUB_WORKLOADS = ("asum", "gemv_square", "gemv_tall", "mixed", "batch")
+
+
+def run_subs(args, rank):
+    """One record per SUB_WORKLOADS entry: K timed steps after W warm-up
+    steps of that workload alone (its own CUDA events, roofline and clock
+    samples), its results against the oracle, and the oracle timed on a
+    short bounded sample of it."""
+    import copy
+    subs = {}
+    for wl in SUB_WORKLOADS:
+        sa = copy.copy(args)
+        sa.workload, sa.no_e2e, sa.no_extras, sa.variant = wl, True, True, None
+        t0 = time.perf_counter()
+        r = run_ours(sa, rank, 1, None)
+        val, sample, _ = oracle_sample(wl, budget_s=3.0)
+        subs[wl] = {
+            "workload": WORKLOADS[wl]["desc"], "value": round(r["value"], 2), "unit": "GB/s",
+            "steps": sa.steps, "warmup": sa.warmup, "ms_per_step": round(r["ms_step"], 5),
+            "frac_of_peak": round(r["value"] / r["peak"], 4), "roofline": r["roofline"],
+            "kernels": {k: {"ms": round(v["ms"], 5), "gbs": round(v["gbs"], 1)}
+                        for k, v in r["per_kernel"].items()},
+            "gpu_launches": r["launches"], "clocks": r["clocks"], "config": r["config"],
+            "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "accuracy_vs_oracle": oracle_accuracy(wl, r["results"])}
+        subs[wl]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return subs
 
 
 def main():
@@ -1022,6 +1136,9 @@ def main():
     ap.add_argument("--mlp", default=None, help="cost-model weights for the batch workload")
     ap.add_argument("--variant", action="append",
                     help="force a variant by name (repeatable), e.g. for a profiling capture")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="dot_scal: skip the records of the other configurations")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the on-the-spot variant sweep and the other submission mode")
     ap.add_argument("--mode", default="batched", choices=["batched", "calls"],
@@ -1068,6 +1185,8 @@ def main():
                            for k, v in res["per_kernel"].items()},
                "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
                "gpu_launches": res["launches"], "accuracy_vs_oracle": accuracy}
+        if world == 1 and args.workload == "dot_scal" and not args.no_sub and not args.variant:
+            out["config"]["sub"] = run_subs(args, rank)
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()

@@ -114,8 +114,11 @@ int lift_sm_count(void);
 
 /* Read (and, if `clear`, reset) the current device's status word, where
  * kernels record a device-side wait that gave up (LIFT_ERR_TIMEOUT).
- * Synchronises with the device.  Returns 0, a lift_status code, or
- * LIFT_ERR_NOT_INITIALIZED / LIFT_ERR_CUDA for the read itself. */
+ * Synchronises with the device.  When `clear` is set and a failure was
+ * recorded, it also waits for the whole device and returns every one-pass
+ * "last CTA" ticket of the workspace to 0 (do not call it then while
+ * another host thread launches on the device).  Returns 0, a lift_status
+ * code, or LIFT_ERR_NOT_INITIALIZED / LIFT_ERR_CUDA for the read itself. */
 int lift_read_status(int clear);
 
 /* ------------------------------------------------------------------------
@@ -484,6 +487,17 @@ lift_status lift_mlp_adam(float* params, const float* grads, float* m, float* v,
  * LIFT_ERR_NOT_INITIALIZED without lift_init. */
 lift_status lift_wait_probe(uint32_t polls, void* stream);
 
+/* Poll limit of the staged (TMA bulk-copy) reductions' wait on each copy
+ * (the paper has no counterpart): 2^22 by default; a failure-detection test
+ * lowers it (0 = give up at the first wait) to drive a real reduction down
+ * its timeout path without a fault.  A reduction whose wait gives up
+ * records LIFT_ERR_TIMEOUT in the status word, waits with the default limit
+ * for its copies still in flight, and still completes its cross-CTA
+ * combine: its result is NaN and the one-pass ticket returns to 0, so the
+ * next call is correct.  Process-wide; applies to launches made after the
+ * call.  Errors: LIFT_ERR_INVALID_ARG for polls above 2^22. */
+lift_status lift_set_wait_polls(uint32_t polls);
+
 /* ------------------------------------------------------------------------
  * Allocation-free asum.  The paper has no counterpart: this entry point
  * exists for callers that must not have the library allocate device memory
@@ -500,8 +514,16 @@ lift_status lift_wait_probe(uint32_t polls, void* stream);
  *  - Every call shares the array.  Each call clears the ticket on `stream`
  *    before its kernel; calls whose kernels overlap on the GPU race and
  *    give wrong results, so order them.
+ *  - x needs 4-byte alignment only, as for lift_asum: a 16-byte aligned x
+ *    is read with 128-bit loads, any other x with 4-byte loads of the same
+ *    elements in the same order (the result is the same).
  *  - A launch that would need more than 4096 partial slots returns
- *    LIFT_ERR_UNSUPPORTED; invalid arguments return LIFT_ERR_INVALID_ARG.
+ *    LIFT_ERR_UNSUPPORTED; invalid arguments (n < 0, a NULL result, a NULL
+ *    x with n > 0, an x not 4-byte aligned) return LIFT_ERR_INVALID_ARG
+ *    before any CUDA call.  n == 0 writes 0.
+ *  - The cached address belongs to the device's context: after
+ *    cudaDeviceReset, call lift_finalize (which forgets it) before the next
+ *    call.
  * ------------------------------------------------------------------------ */
 lift_status lift_asum_noalloc(const float* x, int64_t n, float* result, void* stream);
 

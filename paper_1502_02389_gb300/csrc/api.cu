@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <fstream>
 #include <map>
 #include <mutex>
@@ -23,6 +24,9 @@ lift_status set_error(lift_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
 }
+
+static std::atomic<uint32_t> g_wait_polls{kWaitPolls};
+uint32_t wait_polls() { return g_wait_polls.load(); }
 
 lift_status cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return LIFT_OK;
@@ -369,6 +373,7 @@ extern "C" {
 lift_status lift_init(int device) { return init_device(device); }
 
 lift_status lift_finalize(void) {
+  noalloc_forget();
   std::lock_guard<std::mutex> lk(g_mu);
   int prev = -1;
   cudaGetDevice(&prev);
@@ -413,8 +418,23 @@ int lift_read_status(int clear) {
   int v = 0;
   if (cudaMemcpy(&v, st->ws.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LIFT_ERR_CUDA;
-  if (clear) cudaMemset(st->ws.status, 0, sizeof(int));
+  if (clear && v != 0) {
+    // after a recorded failure, also return every "last CTA" ticket to 0
+    // (a kernel that gave up still takes its ticket, so they should be; this
+    // restores them whatever path the failure took).  Waits for the device.
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemset(st->ws.tickets, 0, kTicketSlots * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(st->ws.status, 0, sizeof(int)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return LIFT_ERR_CUDA;
+  }
   return v;
+}
+
+lift_status lift_set_wait_polls(uint32_t polls) {
+  if (polls > kWaitPolls) return set_error(LIFT_ERR_INVALID_ARG, "wait polls above the default limit");
+  g_wait_polls.store(polls);
+  return LIFT_OK;
 }
 
 lift_status lift_asum_v(int variant, const float* x, int64_t n, float* result, double* result_f64,

@@ -36,8 +36,12 @@ struct DeviceState {
 };
 
 DeviceState* current_state();  // state of the current device, or nullptr
+void noalloc_forget();          // drop lift_asum_noalloc's cached per-device addresses
 
 lift_status set_error(lift_status s, const std::string& msg);
+// Poll limit of the staged reductions' first wait on each copy
+// (lift_set_wait_polls; kWaitPolls unless a test lowers it).
+uint32_t wait_polls();
 lift_status cuda_check(cudaError_t e, const char* what);
 
 // ---------------------------------------------------------------------------
@@ -232,10 +236,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
-// Bounded wait for phase `parity` of `bar`; false after kWaitPolls polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar`; false after `polls` polls
+// (0: gives up at once).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t polls = kWaitPolls) {
   const uint32_t a = smem_addr(bar);
-  for (uint32_t i = 0; i < kWaitPolls; ++i) {
+  for (uint32_t i = 0; i < polls; ++i) {
     uint32_t ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "

@@ -23,23 +23,32 @@
 // cudaGetSymbolAddress (with that device current) and caches it; make that
 // first call before any stream capture.  A launch that would need more
 // partial slots than the array holds is refused with LIFT_ERR_UNSUPPORTED.
+// x needs only 4-byte alignment: a 16-byte aligned x is read with 128-bit
+// loads, any other x element by element in the same order (same result).
+// The cached address belongs to the device's current context: after
+// cudaDeviceReset, call lift_finalize (which forgets it) before the next call.
 #include <mutex>
 
 #include "lift_internal.cuh"
+#include "noalloc_plan.h"
 
 namespace lift {
 namespace {
 
-constexpr int kNoAllocSlots = 4096;
-constexpr int kThreads = 256, kTile = 4096, kVW = 4;
+using noalloc::kThreads;
+using noalloc::kTile;
+using noalloc::kVW;
 
 struct NoAllocScratch {
-  float partials[kNoAllocSlots];
+  float partials[noalloc::kSlots];
   unsigned ticket;
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
+// VEC: full tiles read with 128-bit loads (x 16-byte aligned), else with
+// 4-byte loads of the same elements in the same order.
+template <bool VEC>
 __global__ void __launch_bounds__(kThreads)
     asum_noalloc_kernel(const float* __restrict__ x, int64_t n, NoAllocScratch* scratch,
                         float* result) {
@@ -54,7 +63,15 @@ __global__ void __launch_bounds__(kThreads)
   for (; tile < full; tile += gridDim.x) {
     Vec<kVW> v[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) ld_stream(x + tile * kTile + (int64_t)(t + kThreads * j) * kVW, v[j]);
+    for (int j = 0; j < J; ++j) {
+      const float* p = x + tile * kTile + (int64_t)(t + kThreads * j) * kVW;
+      if constexpr (VEC) {
+        ld_stream(p, v[j]);
+      } else {
+#pragma unroll
+        for (int l = 0; l < kVW; ++l) v[j].v[l] = __ldg(p + l);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < J; ++j)
 #pragma unroll
@@ -88,56 +105,75 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+struct PerDevice {
+  NoAllocScratch* addr = nullptr;
+  int sms = 0, per_sm = 0;   // CTAs per SM of the two forms (the smaller of them)
+};
+
 std::mutex g_mu;
-std::vector<NoAllocScratch*> g_addr;   // per device, filled on first use
-std::vector<int> g_grid;
+std::vector<PerDevice> g_dev;   // per device ordinal, filled on first use
 
 }  // namespace
+
+// Forget the cached per-device addresses (lift_finalize; needed after a
+// cudaDeviceReset, which unloads the module that holds the array).
+void noalloc_forget() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_dev.clear();
+}
+
 }  // namespace lift
 
 using namespace lift;
 
 extern "C" lift_status lift_asum_noalloc(const float* x, int64_t n, float* result, void* stream) {
-  if (n < 0 || !result || (n > 0 && !x) || !aligned(x, 4))
+  noalloc::Plan p;
+  // arguments first, before any CUDA call (the device values do not matter yet)
+  if (noalloc::plan(x, n, result != nullptr, 1, 1, &p) == noalloc::kBadArgs)
     return set_error(LIFT_ERR_INVALID_ARG, "asum_noalloc arguments");
   int dev = -1;
   lift_status rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   if (rc != LIFT_OK) return rc;
-  NoAllocScratch* scratch = nullptr;
-  int per_device_grid = 0;
+  PerDevice d;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if ((int)g_addr.size() <= dev) {
-      g_addr.resize(dev + 1, nullptr);
-      g_grid.resize(dev + 1, 0);
-    }
-    if (!g_addr[dev]) {
+    if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+    if (!g_dev[dev].addr) {
       // set-up, once per device, with that device current
-      void* p = nullptr;
-      rc = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+      void* a = nullptr;
+      rc = cuda_check(cudaGetSymbolAddress(&a, g_noalloc_scratch), "cudaGetSymbolAddress");
       if (rc != LIFT_OK) return rc;
-      int sms = 0, per_sm = 0;
+      int sms = 0, v4 = 0, v1 = 0;
       rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+      if (rc == LIFT_OK)
+        rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &v4, asum_noalloc_kernel<true>, kThreads, 0), "occupancy");
+      if (rc == LIFT_OK)
+        rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &v1, asum_noalloc_kernel<false>, kThreads, 0), "occupancy");
       if (rc != LIFT_OK) return rc;
-      rc = cuda_check(
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, asum_noalloc_kernel, kThreads, 0),
-          "occupancy");
-      if (rc != LIFT_OK) return rc;
-      g_addr[dev] = static_cast<NoAllocScratch*>(p);
-      g_grid[dev] = sms * per_sm;
+      if (sms < 1 || v4 < 1 || v1 < 1)
+        return set_error(LIFT_ERR_CUDA, "asum_noalloc: no CTA of the kernel fits on an SM");
+      g_dev[dev].addr = static_cast<NoAllocScratch*>(a);
+      g_dev[dev].sms = sms;
+      g_dev[dev].per_sm = v4 < v1 ? v4 : v1;
     }
-    scratch = g_addr[dev];
-    per_device_grid = g_grid[dev];
+    d = g_dev[dev];
   }
-  const int64_t tiles = n > 0 ? (n + kTile - 1) / kTile : 1;
-  const int64_t grid = tiles < per_device_grid ? tiles : per_device_grid;
-  if (grid > kNoAllocSlots || grid < 1)
-    return set_error(LIFT_ERR_UNSUPPORTED,
-                     "asum_noalloc: the launch needs more partial slots than its fixed scratch "
-                     "array holds (4096)");
+  switch (noalloc::plan(x, n, true, d.sms, d.per_sm, &p)) {
+    case noalloc::kOk: break;
+    case noalloc::kTooLarge:
+      return set_error(LIFT_ERR_UNSUPPORTED,
+                       "asum_noalloc: the launch needs more partial slots than its fixed scratch "
+                       "array holds (4096)");
+    default: return set_error(LIFT_ERR_INVALID_ARG, "asum_noalloc arguments");
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  rc = cuda_check(cudaMemsetAsync(&scratch->ticket, 0, sizeof(unsigned), s), "ticket clear");
+  rc = cuda_check(cudaMemsetAsync(&d.addr->ticket, 0, sizeof(unsigned), s), "ticket clear");
   if (rc != LIFT_OK) return rc;
-  asum_noalloc_kernel<<<(unsigned)grid, kThreads, 0, s>>>(x, n, scratch, result);
+  if (p.vector_loads)
+    asum_noalloc_kernel<true><<<(unsigned)p.grid, kThreads, 0, s>>>(x, n, d.addr, result);
+  else
+    asum_noalloc_kernel<false><<<(unsigned)p.grid, kThreads, 0, s>>>(x, n, d.addr, result);
   return cuda_check(cudaGetLastError(), "asum_noalloc launch");
 }

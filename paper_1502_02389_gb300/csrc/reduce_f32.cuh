@@ -138,7 +138,7 @@ template <int OP, int THREADS, int TILE, int VW, bool STRIDE, int CLUSTER, bool 
 __global__ void __launch_bounds__(THREADS)
     reduce_ldg(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
                float* __restrict__ partials, unsigned* ticket, float* result, double* result64,
-               int* status) {
+               int* status, uint32_t polls) {
   constexpr int V = TILE / VW, J = V / THREADS;
   static_assert(V % THREADS == 0 && J >= 1, "tile too small for the CTA");
   __shared__ float red[kWarp];
@@ -186,13 +186,14 @@ __global__ void __launch_bounds__(THREADS)
   for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
   finish<OP, THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
   (void)status;
+  (void)polls;
 }
 
 template <int OP, int THREADS, int TILE, int VW, bool STRIDE, int STAGES, int CLUSTER, bool ONEPASS>
 __global__ void __launch_bounds__(THREADS)
     reduce_tma(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
                float* __restrict__ partials, unsigned* ticket, float* result, double* result64,
-               int* status) {
+               int* status, uint32_t polls) {
   constexpr int V = TILE / VW, J = V / THREADS;
   constexpr int NIN = (OP == LIFT_OP_DOT) ? 2 : 1;
   constexpr uint32_t kTileBytes = TILE * sizeof(float);
@@ -227,10 +228,11 @@ __global__ void __launch_bounds__(THREADS)
   float acc[VW];
 #pragma unroll
   for (int l = 0; l < VW; ++l) acc[l] = 0.0f;
+  bool timed_out = false;
   int64_t k = 0;
   for (; k < myK; ++k) {
     const int s = static_cast<int>(k % STAGES);
-    const bool ok = mbar_wait(&full_bar[s], static_cast<uint32_t>((k / STAGES) & 1));
+    const bool ok = mbar_wait(&full_bar[s], static_cast<uint32_t>((k / STAGES) & 1), polls);
     if (ok) {
       const float* bx = buf + (size_t)s * NIN * TILE;
 #pragma unroll
@@ -243,23 +245,29 @@ __global__ void __launch_bounds__(THREADS)
       }
     }
     if (!__syncthreads_and(ok)) {
-      // a copy never completed: record it and drain what is still in flight
+      // a copy did not complete in time: record it, wait (with the full
+      // limit) for every copy still in flight into the ring -- the one
+      // waited for included -- so none lands after the CTA has left, and
+      // stop folding.  The CTA still takes its ticket below with a NaN
+      // partial: the call's result is NaN, and the ticket returns to 0.
       if (t == 0) {
         report(status, LIFT_ERR_TIMEOUT);
-        for (int64_t q = k + 1; q < k + STAGES && q < myK; ++q)
+        for (int64_t q = k; q < k + STAGES && q < myK; ++q)
           mbar_wait(&full_bar[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1));
       }
-      return;
+      timed_out = true;
+      break;
     }
     if (t == 0 && k + STAGES < myK) issue(k + STAGES);
   }
   const int64_t tail_owner = full % G;
-  if (full * TILE < n && (int64_t)blockIdx.x == tail_owner)
+  if (!timed_out && full * TILE < n && (int64_t)blockIdx.x == tail_owner)
     fold_tail<OP, THREADS, TILE, VW, STRIDE>(acc, x, y, n, full);
 
   float r = acc[0];
 #pragma unroll
   for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
+  if (timed_out) r = __int_as_float(0x7fc00000);
   finish<OP, THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
 }
 
@@ -337,7 +345,8 @@ struct ReduceF32 {
     float* result = a.result;
     double* result64 = a.result64;
     int* status = st->ws.status;
-    void* args[] = {&x, &y, &n, &partials, &ticket, &result, &result64, &status};
+    uint32_t polls = wait_polls();
+    void* args[] = {&x, &y, &n, &partials, &ticket, &result, &result64, &status, &polls};
     lift_status rc = launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), CLUSTER, s, args);
     if (rc != LIFT_OK || PASSES == 1) return rc;
     return launch_combine<OP>(partials, g / CLUSTER, a.result, a.result64, s);

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(THREADS)
     if (!__syncthreads_and(ok)) {
       if (t == 0) {
         report(status, LIFT_ERR_TIMEOUT);
-        for (int64_t q = k + 1; q < k + STAGES && q < myK; ++q)
+        for (int64_t q = k; q < k + STAGES && q < myK; ++q)   // every copy still in flight
           mbar_wait(&full_bar[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1));
         bulk_wait_all();
       }

@@ -82,6 +82,7 @@ _SIGS = {
     "lift_nrm2": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_gemv_t": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
     "lift_wait_probe": ([ctypes.c_uint32, _P], ctypes.c_int),
+    "lift_set_wait_polls": ([ctypes.c_uint32], ctypes.c_int),
     "lift_asum_partial": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_dot_partial": ([_P, _P, _I64, _P, _P], ctypes.c_int),
     "lift_combine_partials": ([_P, _I64, _P, _P], ctypes.c_int),
@@ -251,6 +252,10 @@ def lift_combine_partials(partials) -> tuple:
 
 def lift_wait_probe(polls, stream=None):
     _check(lib().lift_wait_probe(polls, _stream(stream)), "lift_wait_probe")
+
+
+def lift_set_wait_polls(polls):
+    _check(lib().lift_set_wait_polls(polls), "lift_set_wait_polls")
 
 
 def lift_asum_comp(x, n, result, result_f64=None, stream=None):

@@ -47,3 +47,79 @@ def test_probe_arguments(L):
         L.lift_wait_probe(0)
     with pytest.raises(L.LiftError):
         L.lift_wait_probe((1 << 22) + 1)
+
+
+def _expected_bits(L, opname, op, vid, x, y):
+    """The variant's low-level expression evaluated in fp32 mode."""
+    from oracle import lowlevel as ll
+    from oracle.patterns import evaluate
+    v = L.lift_variant_describe(op, vid)
+    n = x.size
+    e, Lp = ll.reduce_variant(opname, n, v["tile"], v["vw"], v["threads"],
+                              L.lift_variant_grid(op, vid, n), bool(v["stride"]), v["cluster"],
+                              v["final_threads"])
+    xp = np.zeros(Lp, np.float32)
+    xp[:n] = x
+    if opname != "dot":
+        return np.float32(evaluate(e, xp, mode="f32")[0])
+    yp = np.zeros(Lp, np.float32)
+    yp[:n] = y
+    return np.float32(evaluate(e, (xp, yp), mode="f32")[0])
+
+
+def _run(L, opname, vid, xd, yd, n, r):
+    if opname == "asum":
+        L.lift_asum_v(vid, xd, n, r)
+    elif opname == "dot":
+        L.lift_dot_v(vid, xd, yd, n, r)
+    elif opname == "nrm2":
+        L.lift_nrm2_v(vid, xd, n, r)
+    else:
+        L.lift_sum_v(vid, xd, n, r)
+
+
+def test_staged_reduction_timeout_keeps_the_one_pass_tickets(L):
+    """A real staged reduction driven down its timeout path: with the wait
+    limit at 0 every CTA's first wait on a bulk copy gives up, so the call
+    records LIFT_ERR_TIMEOUT, drains its copies and returns NaN -- and,
+    because every CTA still takes its "last CTA" ticket, the ticket is back
+    at 0.  The very next one-pass asum / dot / nrm2 / sum calls (before the
+    status word is read, so nothing resets the tickets for them) equal their
+    low-level expressions bit for bit."""
+    assert L.lift_read_status(1) == 0
+    n = 70001
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(n).astype(np.float32)
+    y = rng.standard_normal(n).astype(np.float32)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    r = torch.empty(1, device="cuda")
+    ops = (("asum", L.OP_ASUM), ("dot", L.OP_DOT), ("nrm2", L.OP_NRM2), ("sum", L.OP_SUM))
+    staged = [(nm, op, v["id"]) for nm, op in ops for v in L.variants(op)
+              if v["stages"] > 0 and v["passes"] == 1]
+    assert staged
+    L.lift_set_wait_polls(0)
+    try:
+        for nm, op, vid in staged:
+            r.fill_(1.0)
+            _run(L, nm, vid, xd, yd, n, r)
+            torch.cuda.synchronize()
+            assert np.isnan(r.item()), L.lift_variant_describe(op, vid)["name"]
+    finally:
+        L.lift_set_wait_polls(1 << 22)
+    for nm, op in ops:
+        for v in L.variants(op):
+            if v["passes"] != 1:
+                continue
+            r.fill_(-7.0)
+            _run(L, nm, v["id"], xd, yd, n, r)
+            torch.cuda.synchronize()
+            got = np.float32(r.item())
+            assert got == _expected_bits(L, nm, op, v["id"], x, y), v["name"]
+    assert L.lift_read_status(1) == L.ERR_TIMEOUT
+    assert L.lift_read_status(1) == 0
+
+
+def test_wait_polls_arguments(L):
+    with pytest.raises(L.LiftError):
+        L.lift_set_wait_polls((1 << 22) + 1)
+    L.lift_set_wait_polls(1 << 22)

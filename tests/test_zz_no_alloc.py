@@ -44,3 +44,35 @@ def test_noalloc_asum_matches_lift_asum_on_two_calls_in_a_row():
     with pytest.raises(lift.LiftError) as e:
         lift.lift_asum_noalloc(xd[0], -1, got[:1])
     assert e.value.status == lift.ERR_INVALID_ARG
+
+
+def test_noalloc_asum_misaligned_and_empty_inputs():
+    """x may be any 4-byte aligned pointer, as for lift_asum: offsets of 1, 2
+    and 3 floats go to the 4-byte-load form, which folds the same elements
+    in the same order, so its result equals the aligned call's bit for bit
+    and the oracle's within the parity bound.  n == 0 writes exactly 0."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_02389_gb300 import build, lift
+    build.build()
+    torch.cuda.set_device(0)
+    n = (1 << 21) + 4097                                  # ragged: a partial last tile
+    x = synth.asum_small(n, seed=7)
+    aligned = torch.from_numpy(x).cuda()
+    ref = torch.full((1,), -1.0, device="cuda")
+    lift.lift_asum_noalloc(aligned, n, ref)
+    tol = blas.tolerance(n, blas.asum_terms(x))
+    for off in (1, 2, 3):
+        buf = torch.full((n + 8,), float("nan"), device="cuda")
+        view = buf[off:off + n]
+        view.copy_(aligned)
+        assert view.data_ptr() % 16 != 0
+        got = torch.full((1,), -1.0, device="cuda")
+        lift.lift_asum_noalloc(view, n, got)
+        torch.cuda.synchronize()
+        assert float(got) == float(ref), off
+        assert abs(float(got) - blas.asum(x.astype(np.float64))) <= tol
+    zero = torch.full((1,), -1.0, device="cuda")
+    lift.lift_asum_noalloc(aligned, 0, zero)
+    torch.cuda.synchronize()
+    assert float(zero) == 0.0
