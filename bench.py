@@ -773,12 +773,13 @@ def run_ours(args, rank, world, dist):
             "same_step_as_one_batched_launch_gbs"
         config[key] = round(bytes_step * 50 / (a2.elapsed_time(b2) / 1e3) / 1e9, 1)
         lift.lift_batch_destroy(hb2)
-    if wl == "batch":
+    if wl == "batch" and not args.no_extras:
         config["policies_gbs"] = policy_rates()
-        for h in handles.values():
-            lift.lift_batch_destroy(h)
     assert lift.lift_read_status() == 0
     results = collect() if (collect is not None and rank == 0) else None
+    if wl == "batch":
+        for h in handles.values():
+            lift.lift_batch_destroy(h)
     if results is not None and e2e is not None and "result" in e2e:
         results["e2e_dot"] = e2e["result"]
     torch.cuda.synchronize()

@@ -260,14 +260,21 @@ def gemv_split_z_variant(M: int, N: int, alpha, vw: int, threads: int, L: int, S
     return C(Map(mult_by(alpha)), Join(), Map(row))
 
 
-def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int, passes: int = 1):
+def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int, passes: int = 1,
+                     cluster: int = 1):
     """z of the gemv-T kernel: every column of A (the rows of the
     reorder-stride view) zipped with x, padded to RB*B, folded in RB blocks
     of B rows (fp32); the block partials are then combined in fp32 --
-    one pass: added in block order; two pass: lane l of one warp adds
+    one pass: added in block order; one pass with clusters of ``cluster``
+    blocks: each cluster's consecutive block partials added in order, then
+    the cluster sums added in order (the partial reduction of Fig. 3d
+    applied to the block partials); two pass: lane l of one warp adds
     partials l, l+32, ..., then a halving tree over the lanes -- and
     multiplied by alpha."""
-    if passes == 1:
+    if passes == 1 and cluster > 1:
+        assert RB % cluster == 0
+        combine = C(ReduceSeq(add, 0), Join(), Map(ReduceSeq(add, 0)), Split(cluster))
+    elif passes == 1:
         combine = ReduceSeq(add, 0)
     else:
         per = max(1, math.ceil(RB / WARP))

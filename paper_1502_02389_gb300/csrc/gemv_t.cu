@@ -31,7 +31,11 @@
 // part, which made an FP64 combine of the N x RB partials cost as much as
 // streaming A.  The epilogue multiplies by alpha and adds fl(beta * y_j) (y
 // is not read when beta == 0).
+#include <cooperative_groups.h>
+
 #include "lift_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lift {
 
@@ -42,16 +46,12 @@ lift_status launch_rows_combine(int64_t n, int64_t per, float alpha, float beta,
 
 namespace {
 
-template <int THREADS, int VW, int U, int PASSES>
-__global__ void __launch_bounds__(THREADS)
-    gemv_t_kernel(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
-                  const float* __restrict__ x, float beta, float* __restrict__ y, int64_t B,
-                  float* __restrict__ partials, unsigned* __restrict__ tickets) {
-  constexpr int CB = THREADS * VW;
-  const int64_t cb = blockIdx.x, rb = blockIdx.y, RB = gridDim.y;
-  const int64_t c0 = cb * CB + (int64_t)threadIdx.x * VW;
-  const int64_t r0 = rb * B, r1 = (r0 + B < M) ? r0 + B : M;
-  float acc[VW];
+// Row block [r0, r1) of this thread's VW columns c0 .. c0+VW-1, folded in
+// row order into acc (fp32; zero for an empty block).
+template <int VW, int U>
+__device__ __forceinline__ void fold_rows(int64_t N, const float* __restrict__ A, int64_t lda,
+                                          const float* __restrict__ x, int64_t c0, int64_t r0,
+                                          int64_t r1, float* acc) {
 #pragma unroll
   for (int l = 0; l < VW; ++l) acc[l] = 0.f;
   const bool full_cols = c0 + VW <= N;
@@ -85,6 +85,19 @@ __global__ void __launch_bounds__(THREADS)
         if (c0 + l < N) acc[l] = __fadd_rn(acc[l], __fmul_rn(__ldg(A + i * lda + c0 + l), xv));
     }
   }
+}
+
+template <int THREADS, int VW, int U, int PASSES>
+__global__ void __launch_bounds__(THREADS)
+    gemv_t_kernel(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
+                  const float* __restrict__ x, float beta, float* __restrict__ y, int64_t B,
+                  float* __restrict__ partials, unsigned* __restrict__ tickets) {
+  constexpr int CB = THREADS * VW;
+  const int64_t cb = blockIdx.x, rb = blockIdx.y, RB = gridDim.y;
+  const int64_t c0 = cb * CB + (int64_t)threadIdx.x * VW;
+  const int64_t r0 = rb * B, r1 = (r0 + B < M) ? r0 + B : M;
+  float acc[VW];
+  fold_rows<VW, U>(N, A, lda, x, c0, r0, r1, acc);
 
   if constexpr (PASSES == 2) {
     // the combine kernel may start launching; it waits for this grid to end
@@ -158,6 +171,74 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Cluster form (one launch): the RB row blocks of a column block are
+// grouped CL to a thread-block cluster along gridDim.y.  Each CTA folds its
+// block into shared memory; after a cluster barrier, CTA of rank q adds, for
+// the columns of slice q (CB / CL of them), the CL block partials of its
+// cluster in rank (= block) order through distributed shared memory, and
+// writes one partial per column and cluster, P[c][j] (c = rb / CL).  The
+// CTA that arrives last at the ticket of (column block, slice) adds the
+// RB / CL cluster partials of the slice's columns in cluster order (all its
+// loads in flight) and writes y.  Per column:
+//   s = reduce-seq(add, 0) over clusters of reduce-seq(add, 0) over the CL
+//       block partials of the cluster;   y_j = fl(alpha*s) (+ fl(beta*y_j)).
+template <int THREADS, int VW, int U, int CL>
+__global__ void __launch_bounds__(THREADS)
+    gemv_t_cluster(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
+                   const float* __restrict__ x, float beta, float* __restrict__ y, int64_t B,
+                   float* __restrict__ partials, unsigned* __restrict__ tickets) {
+  constexpr int CB = THREADS * VW, SL = CB / CL;
+  static_assert(CB % CL == 0, "a slice holds whole columns");
+  __shared__ __align__(16) float part[CB];
+  __shared__ bool is_last;
+  const int64_t cb = blockIdx.x, rb = blockIdx.y, RB = gridDim.y, RBC = RB / CL;
+  const int64_t c0 = cb * CB + (int64_t)threadIdx.x * VW;
+  const int64_t r0 = rb * B, r1 = (r0 + B < M) ? r0 + B : M;
+  float acc[VW];
+  fold_rows<VW, U>(N, A, lda, x, c0, r0, r1, acc);     // empty past M (padding blocks)
+#pragma unroll
+  for (int l = 0; l < VW; ++l) part[threadIdx.x * VW + l] = acc[l];
+
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();                                    // every block partial of the cluster written
+  const int q = static_cast<int>(cl.block_rank());
+  const int64_t c = rb / CL;
+  for (int k = threadIdx.x; k < SL; k += THREADS) {
+    const int col = q * SL + k;
+    float p = 0.f;
+#pragma unroll
+    for (int r = 0; r < CL; ++r) p = __fadd_rn(p, *cl.map_shared_rank(part + col, r));
+    const int64_t j = cb * CB + col;
+    if (j < N) partials[c * N + j] = p;
+  }
+  cl.sync();                                    // peers done reading this CTA's partials
+  unsigned* ticket = tickets + cb * CL + q;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(ticket, 1u) == static_cast<unsigned>(RBC - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int k = threadIdx.x; k < SL; k += THREADS) {
+    const int64_t j = cb * CB + q * SL + k;
+    if (j >= N) continue;
+    float s = 0.f;
+    int64_t e = 0;
+    for (; e + 16 <= RBC; e += 16) {            // sixteen loads in flight, added in order
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = __ldcg(partials + (e + u) * N + j);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) s = __fadd_rn(s, v[u]);
+    }
+    for (; e < RBC; ++e) s = __fadd_rn(s, __ldcg(partials + e * N + j));
+    const float z = __fmul_rn(alpha, s);
+    y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
+  }
+  if (threadIdx.x == 0) *ticket = 0u;           // ready for the next call
+}
+
 constexpr int kCombineThreads = 256;
 constexpr int64_t kMaxRowBlocks2 = 512;   // two pass: at most 16 partials per lane
 
@@ -211,6 +292,68 @@ struct GemvT {
     lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
     if (r != LIFT_OK || PASSES == 1) return r;
     return launch_rows_combine(N, RB, alpha, beta, partials, y, s);
+  }
+};
+
+template <int THREADS, int VW, int U, int CL>
+struct GemvTCluster {
+  static constexpr int CB = THREADS * VW;
+  static const void* kernel() {
+    return reinterpret_cast<const void*>(&gemv_t_cluster<THREADS, VW, U, CL>);
+  }
+  // (column blocks, row blocks padded to a multiple of CL, rows per block):
+  // about one wave of the persistent size, rounded down to whole clusters
+  static void shape(const Args& a, int64_t& ncb, int64_t& RB, int64_t& B) {
+    ncb = (a.N + CB - 1) / CB;
+    const int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
+    int64_t want = g > ncb ? g / ncb : 1;
+    want = want / CL * CL;
+    DeviceState* st = current_state();
+    const int64_t cap = st ? st->ws.capacity / (a.N > 0 ? a.N : 1) * CL : CL;
+    if (want > cap) want = cap / CL * CL;
+    if (want > a.M) want = a.M;
+    if (want < 1) want = 1;
+    B = (a.M + want - 1) / want;
+    RB = (a.M + B - 1) / B;
+    RB = (RB + CL - 1) / CL * CL;
+  }
+  static int64_t grid(const Variant&, const Args& a) {
+    int64_t ncb, RB, B;
+    shape(a, ncb, RB, B);
+    return ncb * RB;
+  }
+  static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
+    DeviceState* st = current_state();
+    if (a.N == 0) return LIFT_OK;
+    if (a.M == 0) return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t with M == 0 goes through gemv_t_scale");
+    int64_t ncb, RB, B;
+    shape(a, ncb, RB, B);
+    if (ncb * CL > kTicketSlots - kTicketBase)
+      return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: more column slices than tickets");
+    if (RB / CL * a.N > st->ws.capacity)
+      return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: N exceeds the partials workspace");
+    if (RB > 65535) return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: too many row blocks");
+    int64_t M = a.M, N = a.N, lda = a.lda;
+    float alpha = a.alpha, beta = a.beta;
+    const float* A = a.A;
+    const float* x = static_cast<const float*>(a.x);
+    float* y = a.out;
+    float* partials = st->ws.partials;
+    unsigned* tickets = st->ws.tickets + kTicketBase;
+    void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ncb, (unsigned)RB);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CL;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_check(cudaLaunchKernelExC(&cfg, kernel(), args), "gemv_t cluster launch");
   }
 };
 
@@ -286,12 +429,36 @@ lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s) {
   X(128, 8, 4, 2, "t128_v8_u4_p2")   \
   X(64, 4, 8, 2, "t64_v4_u8_p2")
 
+// cluster forms (appended after the others so that variant ids stay put)
+#define LIFT_GEMV_T_CLUSTER_VARIANTS(X) \
+  X(256, 4, 4, 8, "t256_v4_u4_c8")      \
+  X(256, 4, 8, 8, "t256_v4_u8_c8")      \
+  X(256, 4, 4, 4, "t256_v4_u4_c4")      \
+  X(128, 4, 8, 8, "t128_v4_u8_c8")      \
+  X(128, 8, 4, 8, "t128_v8_u4_c8")      \
+  X(64, 4, 8, 8, "t64_v4_u8_c8")
+
+template <int THREADS, int VW, int U, int CL>
+Variant gemv_t_cluster_variant(const char* name) {
+  using K = GemvTCluster<THREADS, VW, U, CL>;
+  Variant v = gemv_t_variant<THREADS, VW, U, 1>(name);
+  v.info.cluster = CL;
+  v.info.tree = 2;
+  v.launch = &K::launch;
+  v.grid = &K::grid;
+  return v;
+}
+
 void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB) {
   int64_t ncb = 0, rb = 0, b = 0;
   int k = 0;
 #define X(T, V, U, P, NAME) \
   if (k++ == id) GemvT<T, V, U, P>::shape(a, ncb, rb, b);
   LIFT_GEMV_T_VARIANTS(X)
+#undef X
+#define X(T, V, U, CL, NAME) \
+  if (k++ == id) GemvTCluster<T, V, U, CL>::shape(a, ncb, rb, b);
+  LIFT_GEMV_T_CLUSTER_VARIANTS(X)
 #undef X
   *B = b;
   *RB = rb;
@@ -300,6 +467,9 @@ void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB) {
 void register_gemv_t(std::vector<Variant>& L) {
 #define X(T, V, U, P, NAME) L.push_back(gemv_t_variant<T, V, U, P>(NAME));
   LIFT_GEMV_T_VARIANTS(X)
+#undef X
+#define X(T, V, U, CL, NAME) L.push_back(gemv_t_cluster_variant<T, V, U, CL>(NAME));
+  LIFT_GEMV_T_CLUSTER_VARIANTS(X)
 #undef X
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }

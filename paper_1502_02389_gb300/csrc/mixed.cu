@@ -15,7 +15,8 @@
 //  * each thread takes E = 4096/THREADS consecutive elements of a block
 //    (coalesced 16/32-byte loads) and sums its E terms with a halving tree
 //    (pairwise, depth log2 E; for fp8 asum this sum is exact: E <= 64 values
-//    on the 2^-9 grid below 2^15 need at most 24 bits);
+//    on the 2^-9 grid below 2^15 need at most 24 bits, so the kernel adds
+//    them in a cheaper order with the same value, see fp8_abs_sum);
 //  * the block sum is multiplied once by the block scale (fp8: s_x, or
 //    s_x * s_y for dot) and added into a (sum, compensation) pair with
 //    Knuth's TwoSum;
@@ -138,9 +139,39 @@ __device__ __forceinline__ float block_scale(const float* xs, const float* ys, i
   }
 }
 
+// fp8 asum: a thread's E <= 64 magnitudes |q| lie on the 2^-9 grid below
+// 448, so every partial sum of them is a multiple of 2^-9 below 2^15 and
+// fits the 24-bit fp32 significand: any order of adding them gives the same
+// exact value as the pairwise tree.  Here the sign bits are cleared on the
+// raw bytes, e4m3 pairs are widened to f16 pairs (exact), and each f16 is
+// added straight into an fp32 accumulator with the mixed-precision
+// add.rn.f32.f16 (no separate f16 -> f32 conversion); four accumulators,
+// one per byte position, are added at the end.
+template <int E>
+__device__ __forceinline__ float fp8_abs_sum(const uint32_t* w) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+  for (int i = 0; i < E / 4; ++i) {
+    const uint32_t m = w[i] & 0x7f7f7f7fu;
+    uint32_t lo, hi;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(lo) : "h"(static_cast<uint16_t>(m)));
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(hi) : "h"(static_cast<uint16_t>(m >> 16)));
+    asm("{ .reg .f16 p, q; mov.b32 {p, q}, %2; add.rn.f32.f16 %0, p, %0; add.rn.f32.f16 %1, q, %1; }"
+        : "+f"(a0), "+f"(a1) : "r"(lo));
+    asm("{ .reg .f16 p, q; mov.b32 {p, q}, %2; add.rn.f32.f16 %0, p, %0; add.rn.f32.f16 %1, q, %1; }"
+        : "+f"(a2), "+f"(a3) : "r"(hi));
+  }
+  return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+}
+
 template <int OP, int DT, int E>
 __device__ __forceinline__ void fold_block(Comp& acc, const Raw<DT, E>& rx, const Raw<DT, E>& ry,
                                            float scale) {
+  if constexpr (OP == LIFT_OP_ASUM && DT == DT_FP8) {
+    static_assert(E <= 64, "the exact-sum argument needs at most 64 terms per thread");
+    two_sum_add(acc, __fmul_rn(fp8_abs_sum<E>(rx.w), scale));
+    return;
+  }
   float vx[E], vy[E];
   decode<DT, E>(rx, vx);
   if constexpr (OP == LIFT_OP_DOT) decode<DT, E>(ry, vy);

@@ -64,8 +64,9 @@ def test_bit_exact_to_expression(L, M, N):
         info = L.lift_variant_describe(L.OP_GEMV_T, vid)
         run = vid if N % info["vw"] == 0 else 0
         B, RB = L.lift_gemv_t_blocks(run, M, N)
-        passes = L.lift_variant_describe(L.OP_GEMV_T, run)["passes"]
-        z = evaluate(ll.gemv_t_z_variant(M, N, 1.25, B, RB, passes), A, mode="f32", env={"x": x})
+        rinfo = L.lift_variant_describe(L.OP_GEMV_T, run)
+        z = evaluate(ll.gemv_t_z_variant(M, N, 1.25, B, RB, rinfo["passes"], rinfo["cluster"]), A,
+                     mode="f32", env={"x": x})
         for beta in (0.5, 0.0):
             exp = z if beta == 0 else evaluate(
                 C(Map(add), Zip()), (z, evaluate(Map(mult_by(beta)), y, mode="f32")), mode="f32")

@@ -315,3 +315,18 @@ def test_gemv_split_variant_expression_exact(M, N, vw, threads, L, S):
     x = rng.integers(-9, 9, N).astype(float)
     z = evaluate(ll.gemv_split_z_variant(M, N, 2.0, vw, threads, L, S), A, env={"x": x})
     assert np.array_equal(z, 2.0 * (A @ x))
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+@pytest.mark.parametrize("M,N,B", [(1, 1, 1), (37, 20, 8), (64, 33, 4), (100, 7, 3)])
+def test_gemv_t_cluster_expression_exact(M, N, B, cluster):
+    # the cluster form pads the block count to whole clusters (blocks of
+    # zero rows); on integer inputs it must still give exactly A^T x -- a
+    # dropped cluster, block or padding mistake would not
+    rng = np.random.default_rng(M * N + cluster)
+    A = rng.integers(-9, 9, (M, N)).astype(float)
+    x = rng.integers(-9, 9, M).astype(float)
+    RB = -(-M // B)
+    RB = -(-RB // cluster) * cluster
+    z = evaluate(ll.gemv_t_z_variant(M, N, 2.0, B, RB, 1, cluster), A, env={"x": x})
+    assert np.array_equal(z, 2.0 * (A.T @ x))
