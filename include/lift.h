@@ -352,14 +352,41 @@ lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float*
  *                      autotuner; nearest shape in log2 size).
  *   LIFT_POLICY_MLP:   the cost model (path: weights file written by the
  *                      trainer); argmin of the predicted times.
+ *   LIFT_POLICY_MLP_TUNE: the cost model with exhaustive timing as its
+ *                      fallback (Sec. 6.2 explores parameter values
+ *                      empirically; Sec. 6.3 names a model-guided search).
+ *                      A call whose shape lies outside the range the model
+ *                      was trained on (the weights file's "box"), or whose
+ *                      two best predicted times are within 3 % of each
+ *                      other, has the model's 3 best candidates timed on
+ *                      its stream (one warm-up, then the median of 3 event-
+ *                      timed launches each; the caller's arrays are only
+ *                      read -- outputs go to scratch, a temporary array of
+ *                      the output's size for scal, axpy, BlackScholes, gemv
+ *                      and gemv-T, allocated and freed around the timing),
+ *                      and the fastest is cached per (op, shape,
+ *                      alignment).  The first such call synchronises with
+ *                      its stream.  A call made while its stream is being
+ *                      captured into a CUDA graph, lift_pick and the batch
+ *                      never time: they use a cached winner or the plain
+ *                      learned pick.  Loading weights clears the cache.
  * Both learned policies choose only among the variants that run as
  * themselves on the call's arguments (vector loads need the pointers and,
  * for gemv and gemv-T, the row pitch aligned to the vector width); an
  * explicit or FIXED variant that cannot runs its guarded fallback.
  * ------------------------------------------------------------------------ */
-typedef enum { LIFT_POLICY_FIXED = 0, LIFT_POLICY_TABLE = 1, LIFT_POLICY_MLP = 2 } lift_policy;
+typedef enum {
+  LIFT_POLICY_FIXED = 0,
+  LIFT_POLICY_TABLE = 1,
+  LIFT_POLICY_MLP = 2,
+  LIFT_POLICY_MLP_TUNE = 3
+} lift_policy;
 
 lift_status lift_set_policy(int policy, const char* path);
+/* LIFT_POLICY_MLP_TUNE bookkeeping: shapes whose winner is cached, and the
+ * launches timed so far (both since the process started; either pointer
+ * may be NULL).  Host-only. */
+lift_status lift_tune_stats(int64_t* tuned_shapes, int64_t* timed_launches);
 /* Force `variant` for `op` (-1 clears the override). */
 lift_status lift_set_variant(int op, int variant);
 /* The variant the current policy would use for a dense call (aligned

@@ -171,15 +171,37 @@ class Trainer:
         return self.p.cpu().numpy()
 
 
-def save(path: str, params: np.ndarray, V: int, off: Optional[List[int]] = None) -> None:
-    """Weights file read by lift_set_policy(LIFT_POLICY_MLP, path); ``off``
-    are the output slices of the training data (``offsets(records)``)."""
+def box(records: List[Dict]) -> Dict[int, Tuple[float, ...]]:
+    """Per op, the trained range in log2(size + 1): (lo, hi) of n (M*N for
+    gemv and gemv-T), of M and of N -- what LIFT_POLICY_MLP_TUNE treats as
+    inside the model's experience."""
+    out = {}
+    for op in sorted({r["op"] for r in records}):
+        rs = [r for r in records if r["op"] == op]
+        mat = op in (lift.OP_GEMV, lift.OP_GEMV_T)
+        cols = [[math.log2((r["M"] * r["N"] if mat else r["n"]) + 1) for r in rs],
+                [math.log2(r["M"] + 1) for r in rs], [math.log2(r["N"] + 1) for r in rs]]
+        out[op] = tuple(v for c in cols for v in (min(c), max(c)))
+    return out
+
+
+def save(path: str, params: np.ndarray, V: int, off: Optional[List[int]] = None,
+         records: Optional[List[Dict]] = None) -> None:
+    """Weights file read by lift_set_policy(LIFT_POLICY_MLP[_TUNE], path);
+    ``off`` are the output slices of the training data
+    (``offsets(records)``); with the training records, the trained range of
+    each op is appended ("box")."""
     if off is None:
         off, _ = offsets()
     with open(path, "w") as f:
         f.write(f"lift-mlp 2 {D_IN} {H1} {H2} {V}\n")
         f.write(f"offsets {len(off)} " + " ".join(str(o) for o in off) + "\n")
         f.write(" ".join(f"{x:.9g}" for x in params.tolist()) + "\n")
+        if records:
+            b = box(records)
+            f.write(f"box {len(b)}\n")
+            for op, v in b.items():
+                f.write(f"{op} " + " ".join(f"{x:.6f}" for x in v) + "\n")
 
 
 # ---------------------------------------------------------------------------
@@ -268,7 +290,7 @@ def main():
     t0 = time.perf_counter()
     hist = trainer.train(a.steps, a.lr, log_every=max(1, a.steps // 10))
     train_s = time.perf_counter() - t0      # train() ends with a device synchronise
-    save(a.out, trainer.params(), V, off)
+    save(a.out, trainer.params(), V, off, tr + wl)
     res = evaluate_policies(tr + wl, ho, a.out, a.out + ".table")
     if wl:
         res["workloads"] = summary(regrets(wl, lambda op, n, M, N: _mlp_pick(a.out, op, n, M, N)))

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <sstream>
+#include <tuple>
 
 #include "lift_internal.cuh"
 
@@ -190,7 +191,13 @@ struct TableEntry {
   int variant;
 };
 
+struct Box {                         // trained range of one op, in log2(size + 1)
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // n (M*N for matrices), M, N
+  bool known = false;
+};
+
 struct Mlp {
+  Box box[LIFT_NUM_OPS];
   int d_in = 0, h1 = 0, h2 = 0, V = 0;
   int ops = 0;                       // op ids 0 .. ops-1 have an output slice
   int offsets[LIFT_MLP_OPS] = {0};
@@ -271,9 +278,9 @@ static bool eligible(int op, const Variant& v, const Args& a) {
   return ok;
 }
 
-// The learned pick: the variant with the smallest predicted time among those
-// that run as themselves on these arguments.
-static int mlp_pick(int op, const Args& a) {
+// The learned ranking: (predicted log-time, variant) of every variant that
+// runs as itself on these arguments, fastest first; the pick is the first.
+static std::vector<std::pair<float, int>> mlp_rank(int op, const Args& a) {
   const Mlp& m = g_mlp;
   float f[LIFT_NUM_FEATURES];
   lift_features(op, a.n, a.M, a.N, f);
@@ -293,20 +300,25 @@ static int mlp_pick(int op, const Args& a) {
   const int file_cnt = (op + 1 < m.ops ? m.offsets[op + 1] : m.V) - m.offsets[op];
   const auto& L = registry(op);
   const int cnt = std::min((int)L.size(), file_cnt);
-  int best = -1;                      // none: the caller falls back to the FIXED choice
-  float best_t = INFINITY;
+  std::vector<std::pair<float, int>> r;   // empty: the caller falls back to the FIXED choice
   for (int v = 0; v < cnt; ++v) {
     const int o = m.offsets[op] + v;
     if (o >= m.V) break;
     if (!eligible(op, L[v], a)) continue;
     float s = m.b3[o];
     for (int i = 0; i < m.h2; ++i) s += h2[i] * m.W3[i * m.V + o];
-    if (s < best_t) {
-      best_t = s;
-      best = v;
-    }
+    r.emplace_back(s, v);
   }
-  return best;
+  std::stable_sort(r.begin(), r.end(),
+                   [](const std::pair<float, int>& p, const std::pair<float, int>& q) {
+                     return p.first < q.first;
+                   });
+  return r;
+}
+
+static int mlp_pick(int op, const Args& a) {
+  const auto r = mlp_rank(op, a);
+  return r.empty() ? -1 : r[0].second;
 }
 
 // The tuned table: the variant of the nearest tuned shape (log sizes) among
@@ -331,11 +343,148 @@ static int table_pick(int op, const Args& a) {
   return v;
 }
 
-static int pick_variant(int op, const Args& a) {
+// ---------------------------------------------------------------------------
+// MLP_TUNE: the learned pick, with exhaustive timing of the model's best
+// candidates as its fallback where the model is unsure -- a call outside the
+// box of shapes it was trained on, or one whose two best predicted times are
+// within kTuneMargin of each other.  Outside stream capture the top
+// kTuneTopK candidates are timed once on the call's own stream (one warm-up
+// launch, then the median of kTuneReps event-timed launches; outputs go to
+// scratch, so the caller's arrays are only read), and the winner is cached
+// per (op, shape, alignment).  Inside capture, and in lift_pick, nothing is
+// timed: a cached winner or the plain learned pick is used.
+// ---------------------------------------------------------------------------
+constexpr float kTuneMargin = 0.03f;   // in predicted log-time: about 3 %
+constexpr int kTuneTopK = 3;
+constexpr int kTuneReps = 3;
+constexpr double kBoxSlack = 0.1;      // log2 units beyond the trained range still inside
+
+struct TuneKey {
+  int op;
+  int64_t n, M, N;
+  int align;   // which of the op's variants run as themselves (their eligibility bits)
+  bool operator<(const TuneKey& o) const {
+    return std::tie(op, n, M, N, align) < std::tie(o.op, o.n, o.M, o.N, o.align);
+  }
+};
+static std::map<TuneKey, int> g_tuned;
+static int64_t g_tune_launches = 0;
+
+static bool in_box(int op, const Args& a) {
+  const Box& b = g_mlp.box[op];
+  if (!b.known) return true;
+  const bool matrix = op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T;
+  const double v[3] = {log2((double)(matrix ? a.M * a.N : a.n) + 1.0), log2((double)a.M + 1.0),
+                       log2((double)a.N + 1.0)};
+  for (int i = 0; i < (matrix ? 3 : 1); ++i)
+    if (v[i] < b.lo[i] - kBoxSlack || v[i] > b.hi[i] + kBoxSlack) return false;
+  return true;
+}
+
+static int eligibility_bits(int op, const Args& a) {
+  const auto& L = registry(op);
+  int bits = 0, k = 0;
+  for (const auto& v : L) {
+    if (eligible(op, v, a)) bits |= 1 << (k % 30);
+    ++k;
+  }
+  return bits;
+}
+
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return true;       // unknown: do not time
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Time the candidates on stream s; returns the fastest, or -1 on any error.
+static int tune_candidates(int op, const Args& a0, const std::vector<int>& cand, cudaStream_t s) {
+  DeviceState* st = current_state();
+  if (!st || cand.empty()) return -1;
+  Args a = a0;
+  // outputs to scratch: reductions write their scalar to the workspace's
+  // spare slot; writing ops get a temporary output array
+  int64_t outs = 0;
+  if (op == LIFT_OP_SCAL || op == LIFT_OP_AXPY) outs = a.n;
+  if (op == LIFT_OP_BLACKSCHOLES) outs = 2 * a.n;
+  if (op == LIFT_OP_GEMV) outs = a.M;
+  if (op == LIFT_OP_GEMV_T) outs = a.N;
+  float* scratch = nullptr;
+  if (outs > 0) {
+    if (cudaMalloc(&scratch, outs * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    if (op == LIFT_OP_AXPY) a.y = scratch;     // y is read and written in place
+    a.out = scratch;
+    if (op == LIFT_OP_BLACKSCHOLES) a.result = scratch + a.n;
+  } else {
+    a.result = st->ws.partials + (st->ws.capacity - 1);
+    a.result64 = nullptr;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = -1;
+  float best_ms = INFINITY;
+  bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  const auto& L = registry(op);
+  for (size_t c = 0; ok && c < cand.size(); ++c) {
+    const Variant& v = L[cand[c]];
+    ok = v.launch(v, a, s) == LIFT_OK;                        // warm-up
+    float t[kTuneReps];
+    for (int r = 0; ok && r < kTuneReps; ++r) {
+      ok = cudaEventRecord(e0, s) == cudaSuccess && v.launch(v, a, s) == LIFT_OK &&
+           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&t[r], e0, e1) == cudaSuccess;
+    }
+    g_tune_launches += 1 + kTuneReps;
+    if (!ok) break;
+    std::sort(t, t + kTuneReps);
+    if (t[kTuneReps / 2] < best_ms) {
+      best_ms = t[kTuneReps / 2];
+      best = cand[c];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (scratch) {
+    cudaStreamSynchronize(s);
+    cudaFree(scratch);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    return -1;
+  }
+  return best;
+}
+
+static int pick_variant(int op, const Args& a, cudaStream_t s = nullptr, bool may_tune = false) {
   std::lock_guard<std::mutex> lk(g_policy_mu);
   if (g_override[op] >= 0) return g_override[op];
   int v = -1;
   if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < g_mlp.ops) v = mlp_pick(op, a);
+  if (g_policy == LIFT_POLICY_MLP_TUNE && g_mlp.V > 0 && op < g_mlp.ops) {
+    const auto r = mlp_rank(op, a);
+    if (!r.empty()) {
+      v = r[0].second;
+      const TuneKey key{op, a.n, a.M, a.N, eligibility_bits(op, a)};
+      auto it = g_tuned.find(key);
+      if (it != g_tuned.end()) {
+        v = it->second;
+      } else if (may_tune && r.size() > 1 &&
+                 (!in_box(op, a) || r[1].first - r[0].first < kTuneMargin) && !capturing(s)) {
+        std::vector<int> cand;
+        for (size_t i = 0; i < r.size() && (int)i < kTuneTopK; ++i) cand.push_back(r[i].second);
+        const int w = tune_candidates(op, a, cand, s);
+        if (w >= 0) {
+          g_tuned[key] = w;
+          v = w;
+        }
+      }
+    }
+  }
   if (g_policy == LIFT_POLICY_TABLE) v = table_pick(op, a);
   if (v < 0) v = find_variant(op, kDefaultName[op]);
   return v;
@@ -343,12 +492,13 @@ static int pick_variant(int op, const Args& a) {
 
 // Resolve the variant to run: explicit id or policy pick, then the guarded
 // form when a pointer is not aligned for the chosen variant.
-static lift_status resolve(int op, int variant, const Args& a, const Variant** out) {
+static lift_status resolve(int op, int variant, const Args& a, const Variant** out,
+                           cudaStream_t s = nullptr, bool may_tune = false) {
   auto& L = registry(op);
   if (L.empty()) return set_error(LIFT_ERR_UNSUPPORTED, "no variants for op");
   if (variant < -1 || variant >= (int)L.size())
     return set_error(LIFT_ERR_INVALID_ARG, "variant id out of range");
-  if (variant < 0) variant = pick_variant(op, a);
+  if (variant < 0) variant = pick_variant(op, a, s, may_tune);
   const Variant* v = &L[variant];
   if (!eligible(op, *v, a) && v->fallback >= 0) v = &L[v->fallback];
   *out = v;
@@ -359,7 +509,7 @@ static lift_status run(int op, int variant, const Args& a, void* stream) {
   DeviceState* st = current_state();
   if (!st) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
   const Variant* v = nullptr;
-  lift_status rc = resolve(op, variant, a, &v);
+  lift_status rc = resolve(op, variant, a, &v, static_cast<cudaStream_t>(stream), true);
   if (rc != LIFT_OK) return rc;
   return v->launch(*v, a, static_cast<cudaStream_t>(stream));
 }
@@ -844,7 +994,7 @@ lift_status lift_set_policy(int policy, const char* path) {
     g_policy = policy;
     return LIFT_OK;
   }
-  if (policy == LIFT_POLICY_MLP) {
+  if (policy == LIFT_POLICY_MLP || policy == LIFT_POLICY_MLP_TUNE) {
     Mlp m;
     std::string tag, off;
     int ver;
@@ -867,12 +1017,36 @@ lift_status lift_set_policy(int policy, const char* path) {
     if (!rd(m.W1, (size_t)m.d_in * m.h1) || !rd(m.b1, m.h1) || !rd(m.W2, (size_t)m.h1 * m.h2) ||
         !rd(m.b2, m.h2) || !rd(m.W3, (size_t)m.h2 * m.V) || !rd(m.b3, m.V))
       return set_error(LIFT_ERR_INVALID_ARG, "truncated MLP weights");
+    // optional: the trained range per op ("box <ops>" then op lo_n hi_n lo_M hi_M lo_N hi_N)
+    std::string btag;
+    int nb = 0;
+    if (f >> btag) {
+      if (btag != "box" || !(f >> nb) || nb < 0 || nb > LIFT_NUM_OPS)
+        return set_error(LIFT_ERR_INVALID_ARG, "bad MLP box");
+      for (int i = 0; i < nb; ++i) {
+        int op;
+        Box b;
+        if (!(f >> op >> b.lo[0] >> b.hi[0] >> b.lo[1] >> b.hi[1] >> b.lo[2] >> b.hi[2]) ||
+            op < 0 || op >= LIFT_NUM_OPS)
+          return set_error(LIFT_ERR_INVALID_ARG, "bad MLP box");
+        b.known = true;
+        m.box[op] = b;
+      }
+    }
     std::lock_guard<std::mutex> lk(g_policy_mu);
     g_mlp = m;
     g_policy = policy;
+    g_tuned.clear();
     return LIFT_OK;
   }
   return set_error(LIFT_ERR_INVALID_ARG, "unknown policy");
+}
+
+lift_status lift_tune_stats(int64_t* tuned_shapes, int64_t* timed_launches) {
+  std::lock_guard<std::mutex> lk(g_policy_mu);
+  if (tuned_shapes) *tuned_shapes = (int64_t)g_tuned.size();
+  if (timed_launches) *timed_launches = g_tune_launches;
+  return LIFT_OK;
 }
 
 lift_status lift_pick(int op, int64_t n, int64_t M, int64_t N, int* variant) {

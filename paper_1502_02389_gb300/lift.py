@@ -26,7 +26,7 @@ MLP_OPS = 15    # op ids a cost model can cover (all of them)
 NUM_FEATURES = 12   # lift_features output length
 OP_NAMES = ["asum", "dot", "scal", "gemv", "asum_bf16", "dot_bf16", "asum_fp8", "dot_fp8", "nrm2",
             "sum", "axpy", "gemv_t", "blackscholes", "asum_comp", "dot_comp"]
-POLICY_FIXED, POLICY_TABLE, POLICY_MLP = 0, 1, 2
+POLICY_FIXED, POLICY_TABLE, POLICY_MLP, POLICY_MLP_TUNE = 0, 1, 2, 3
 
 
 class LiftError(RuntimeError):
@@ -83,6 +83,7 @@ _SIGS = {
     "lift_gemv_t": ([_I64, _I64, ctypes.c_float, _P, _I64, _P, ctypes.c_float, _P, _P], ctypes.c_int),
     "lift_wait_probe": ([ctypes.c_uint32, _P], ctypes.c_int),
     "lift_set_wait_polls": ([ctypes.c_uint32], ctypes.c_int),
+    "lift_tune_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "lift_asum_partial": ([_P, _I64, _P, _P], ctypes.c_int),
     "lift_dot_partial": ([_P, _P, _I64, _P, _P], ctypes.c_int),
     "lift_combine_partials": ([_P, _I64, _P, _P], ctypes.c_int),
@@ -252,6 +253,13 @@ def lift_combine_partials(partials) -> tuple:
 
 def lift_wait_probe(polls, stream=None):
     _check(lib().lift_wait_probe(polls, _stream(stream)), "lift_wait_probe")
+
+
+def lift_tune_stats() -> tuple:
+    """(shapes with a cached timed winner, launches timed so far)."""
+    a, b = _I64(), _I64()
+    _check(lib().lift_tune_stats(ctypes.byref(a), ctypes.byref(b)), "lift_tune_stats")
+    return a.value, b.value
 
 
 def lift_set_wait_polls(polls):

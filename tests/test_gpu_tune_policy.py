@@ -1,0 +1,121 @@
+"""LIFT_POLICY_MLP_TUNE on the GPU: the learned pick with exhaustive timing
+of the model's best candidates as its fallback.
+
+* A call made while its stream is captured into a CUDA graph times nothing;
+  the same call outside capture times the candidates once and caches the
+  winner; later calls reuse it.
+* On shapes beyond the trained range (vectors of 2^29 elements and more,
+  matrices of 2^29 entries or with a side longer than any trained one),
+  every variant is timed exhaustively and the regret t(pick) / t(best) of
+  the fallback's pick is compared with the plain learned pick's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_02389_gb300 import build, lift
+    build.build()
+    torch.cuda.set_device(0)
+    lift.lift_init(0)
+    yield lift
+    lift.lift_set_policy(lift.POLICY_FIXED)
+    torch.cuda.synchronize()
+    assert lift.lift_read_status() == 0
+
+
+def test_capture_time_call_does_no_timing(L):
+    from paper_1502_02389_gb300 import costmodel
+    n = (1 << 29) + 4096                 # beyond the trained range of asum (n <= 2^28)
+    x = torch.full((n,), -0.5, device="cuda")
+    r = torch.zeros(2, device="cuda")
+    L.lift_set_policy(L.POLICY_MLP_TUNE, costmodel.WEIGHTS)
+    before = L.lift_tune_stats()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        L.lift_asum(x, n, r[0:1])
+    assert L.lift_tune_stats() == before             # captured: nothing timed
+    g.replay()
+    torch.cuda.synchronize()
+    assert r[0].item() == 0.5 * n                     # exact: every partial sum is
+    L.lift_asum(x, n, r[1:2])                         # outside capture: timed once
+    torch.cuda.synchronize()
+    after = L.lift_tune_stats()
+    assert after[0] == before[0] + 1 and after[1] > before[1]
+    assert r[1].item() == 0.5 * n
+    L.lift_asum(x, n, r[1:2])                         # cached winner: no more timing
+    torch.cuda.synchronize()
+    assert L.lift_tune_stats() == after
+    del g
+
+
+def _buffers(L, op, n, M, N):
+    """(call through the policy, call of variant v) on fresh device arrays."""
+    f = lambda k: torch.randn(k, device="cuda")  # noqa: E731
+    r = torch.zeros(1, device="cuda")
+    if op in (L.OP_ASUM, L.OP_NRM2, L.OP_SUM):
+        x = f(n)
+        pol = {L.OP_ASUM: L.lift_asum, L.OP_NRM2: L.lift_nrm2, L.OP_SUM: L.lift_sum}[op]
+        var = {L.OP_ASUM: L.lift_asum_v, L.OP_NRM2: L.lift_nrm2_v, L.OP_SUM: L.lift_sum_v}[op]
+        return (lambda: pol(x, n, r)), (lambda v: (lambda: var(v, x, n, r)))
+    if op == L.OP_DOT:
+        x, y = f(n), f(n)
+        return (lambda: L.lift_dot(x, y, n, r)), (lambda v: (lambda: L.lift_dot_v(v, x, y, n, r)))
+    if op == L.OP_SCAL:
+        x, y = f(n), torch.empty(n, device="cuda")
+        return (lambda: L.lift_scal(n, 1.5, x, y)), \
+            (lambda v: (lambda: L.lift_scal_v(v, n, 1.5, x, y)))
+    if op == L.OP_AXPY:
+        x, y = f(n), f(n)
+        return (lambda: L.lift_axpy(n, 0.5, x, y)), \
+            (lambda v: (lambda: L.lift_axpy_v(v, n, 0.5, x, y)))
+    A = f(M * N)
+    if op == L.OP_GEMV:
+        x, y = f(N), f(M)
+        return (lambda: L.lift_gemv(M, N, 1.0, A, N, x, 0.5, y)), \
+            (lambda v: (lambda: L.lift_gemv_v(v, M, N, 1.0, A, N, x, 0.5, y)))
+    x, y = f(M), f(N)
+    return (lambda: L.lift_gemv_t(M, N, 1.0, A, N, x, 0.5, y)), \
+        (lambda v: (lambda: L.lift_gemv_t_v(v, M, N, 1.0, A, N, x, 0.5, y)))
+
+
+def test_fallback_regret_beyond_the_trained_range(L):
+    from paper_1502_02389_gb300 import costmodel, tune
+    shapes = [(L.OP_ASUM, (1 << 29) + 12345, 0, 0), (L.OP_DOT, 1 << 29, 0, 0),
+              (L.OP_NRM2, 3 << 28, 0, 0), (L.OP_SUM, (1 << 29) + 1, 0, 0),
+              (L.OP_SCAL, 1 << 29, 0, 0), (L.OP_AXPY, 5 << 27, 0, 0),
+              (L.OP_GEMV, 20000 * 20000, 20000, 20000), (L.OP_GEMV, 1 << 29, 1 << 19, 1 << 10),
+              (L.OP_GEMV_T, 1 << 29, 1 << 15, 1 << 14), (L.OP_GEMV_T, 1 << 29, 1 << 20, 1 << 9)]
+    timer = tune.Timer()
+    rows = []
+    for op, n, M, N in shapes:
+        policy_call, variant_call = _buffers(L, op, n, M, N)
+        L.lift_set_policy(L.POLICY_FIXED)
+        times = {v: timer.per_call_ms([variant_call(v)], 5, 1)
+                 for v in range(L.lift_variant_count(op))}
+        L.lift_set_policy(L.POLICY_MLP, costmodel.WEIGHTS)
+        plain = L.lift_pick(op, n, M, N)
+        L.lift_set_policy(L.POLICY_MLP_TUNE, costmodel.WEIGHTS)
+        policy_call()                                 # times the candidates (beyond the box)
+        torch.cuda.synchronize()
+        tuned = L.lift_pick(op, n, M, N)              # the cached winner
+        best = min(times.values())
+        rows.append((L.OP_NAMES[op], n, M, N, times[plain] / best, times[tuned] / best))
+        del policy_call, variant_call
+        torch.cuda.empty_cache()
+    L.lift_set_policy(L.POLICY_FIXED)
+    gm = lambda k: math.exp(np.mean([math.log(r[k]) for r in rows]))  # noqa: E731
+    for r in rows:
+        print("%-7s n=%d M=%d N=%d  plain %.4f  tuned %.4f" % r)
+    print(f"geomean regret: plain learned pick {gm(4):.4f}, with the timing fallback {gm(5):.4f}")
+    assert gm(5) <= gm(4) + 1e-9
+    assert gm(5) <= 1.05
