@@ -358,18 +358,22 @@ lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float*
  *                      A call whose shape lies outside the range the model
  *                      was trained on (the weights file's "box"), or whose
  *                      two best predicted times are within 3 % of each
- *                      other, has the model's 3 best candidates timed on
- *                      its stream (one warm-up, then the median of 3 event-
- *                      timed launches each; the caller's arrays are only
- *                      read -- outputs go to scratch, a temporary array of
- *                      the output's size for scal, axpy, BlackScholes, gemv
- *                      and gemv-T, allocated and freed around the timing),
- *                      and the fastest is cached per (op, shape,
- *                      alignment).  The first such call synchronises with
- *                      its stream.  A call made while its stream is being
- *                      captured into a CUDA graph, lift_pick and the batch
- *                      never time: they use a cached winner or the plain
- *                      learned pick.  Loading weights clears the cache.
+ *                      other and whose inputs span at least twice the L2,
+ *                      has its candidates timed -- the model's 3 best, the
+ *                      FIXED default and any variant newer than the model
+ *                      -- each as a CUDA graph of 4 back-to-back launches
+ *                      replayed 5 times (candidates interleaved, median),
+ *                      on a private stream that first waits for the call's
+ *                      stream.  The caller's arrays are only read: outputs
+ *                      go to scratch (a temporary array of the output's
+ *                      size for scal, axpy, BlackScholes, gemv and gemv-T,
+ *                      allocated and freed around the timing).  The fastest
+ *                      is cached per (op, shape, alignment); the first such
+ *                      call waits for the timing.  A call made while its
+ *                      stream is being captured into a CUDA graph,
+ *                      lift_pick and the batch never time: they use a
+ *                      cached winner or the plain learned pick.  Loading
+ *                      weights clears the cache.
  * Both learned policies choose only among the variants that run as
  * themselves on the call's arguments (vector loads need the pointers and,
  * for gemv and gemv-T, the row pitch aligned to the vector width); an

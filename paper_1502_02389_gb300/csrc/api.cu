@@ -2,6 +2,7 @@
 // variant registry and policy, and the extern "C" entry points.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -344,19 +345,24 @@ static int table_pick(int op, const Args& a) {
 }
 
 // ---------------------------------------------------------------------------
-// MLP_TUNE: the learned pick, with exhaustive timing of the model's best
-// candidates as its fallback where the model is unsure -- a call outside the
-// box of shapes it was trained on, or one whose two best predicted times are
-// within kTuneMargin of each other.  Outside stream capture the top
-// kTuneTopK candidates are timed once on the call's own stream (one warm-up
-// launch, then the median of kTuneReps event-timed launches; outputs go to
-// scratch, so the caller's arrays are only read), and the winner is cached
-// per (op, shape, alignment).  Inside capture, and in lift_pick, nothing is
+// MLP_TUNE: the learned pick, with exhaustive timing of candidates as its
+// fallback where the model is unsure -- a call outside the box of shapes it
+// was trained on, or (for working sets of at least twice the L2, which the
+// timing reads cold like the autotuner does) one whose two best predicted
+// times are within kTuneMargin of each other.  The candidates are the
+// model's kTuneTopK best, the FIXED default and every variant added to the
+// library after the model was trained; each is timed as the autotuner times
+// (a CUDA graph of kTuneCalls back-to-back launches, replayed kTuneReps
+// times, the candidates interleaved, median per candidate) on a private
+// stream that waits for the call's stream, with the outputs sent to scratch
+// so the caller's arrays are only read.  The winner is cached per (op,
+// shape, alignment).  Inside stream capture, and in lift_pick, nothing is
 // timed: a cached winner or the plain learned pick is used.
 // ---------------------------------------------------------------------------
 constexpr float kTuneMargin = 0.03f;   // in predicted log-time: about 3 %
 constexpr int kTuneTopK = 3;
-constexpr int kTuneReps = 3;
+constexpr int kTuneCalls = 4;
+constexpr int kTuneReps = 5;
 constexpr double kBoxSlack = 0.1;      // log2 units beyond the trained range still inside
 
 struct TuneKey {
@@ -381,6 +387,23 @@ static bool in_box(int op, const Args& a) {
   return true;
 }
 
+// Bytes the call reads (its inputs): what decides whether repeated timing
+// reads cold data.
+static double input_bytes(int op, const Args& a) {
+  switch (op) {
+    case LIFT_OP_GEMV:
+    case LIFT_OP_GEMV_T: return 4.0 * a.M * a.N;
+    case LIFT_OP_DOT:
+    case LIFT_OP_DOT_COMP:
+    case LIFT_OP_AXPY: return 8.0 * a.n;
+    case LIFT_OP_ASUM_BF16: return 2.0 * a.n;
+    case LIFT_OP_DOT_BF16: return 4.0 * a.n;
+    case LIFT_OP_ASUM_FP8: return 1.0 * a.n;
+    case LIFT_OP_DOT_FP8: return 2.0 * a.n;
+    default: return 4.0 * a.n;
+  }
+}
+
 static int eligibility_bits(int op, const Args& a) {
   const auto& L = registry(op);
   int bits = 0, k = 0;
@@ -389,6 +412,16 @@ static int eligibility_bits(int op, const Args& a) {
     ++k;
   }
   return bits;
+}
+
+static double l2_bytes() {
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return (double)l2;
 }
 
 static bool capturing(cudaStream_t s) {
@@ -400,7 +433,7 @@ static bool capturing(cudaStream_t s) {
   return st != cudaStreamCaptureStatusNone;
 }
 
-// Time the candidates on stream s; returns the fastest, or -1 on any error.
+// Time the candidates; returns the fastest, or -1 on any error.
 static int tune_candidates(int op, const Args& a0, const std::vector<int>& cand, cudaStream_t s) {
   DeviceState* st = current_state();
   if (!st || cand.empty()) return -1;
@@ -425,34 +458,63 @@ static int tune_candidates(int op, const Args& a0, const std::vector<int>& cand,
     a.result = st->ws.partials + (st->ws.capacity - 1);
     a.result64 = nullptr;
   }
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const auto& L = registry(op);
+  const size_t C = cand.size();
+  std::vector<cudaGraphExec_t> exec(C, nullptr);
+  std::vector<std::vector<float>> t(C);
+  cudaStream_t p = nullptr;
+  cudaEvent_t ready = nullptr, e0 = nullptr, e1 = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&p, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&ready) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess && cudaEventRecord(ready, s) == cudaSuccess &&
+            cudaStreamWaitEvent(p, ready, 0) == cudaSuccess;
+  for (size_t c = 0; ok && c < C; ++c) {
+    const Variant& v = L[cand[c]];
+    ok = v.launch(v, a, p) == LIFT_OK;                   // warm-up: loads the kernel
+    cudaGraph_t g = nullptr;
+    ok = ok && cudaStreamBeginCapture(p, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      bool launched = true;
+      for (int k = 0; k < kTuneCalls && launched; ++k) launched = v.launch(v, a, p) == LIFT_OK;
+      ok = cudaStreamEndCapture(p, &g) == cudaSuccess && launched;
+    }
+    ok = ok && cudaGraphInstantiate(&exec[c], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    ok = ok && cudaGraphLaunch(exec[c], p) == cudaSuccess;   // warm-up replay
+    g_tune_launches += 1 + kTuneCalls;
+  }
+  for (int r = 0; ok && r < kTuneReps; ++r)
+    for (size_t c = 0; ok && c < C; ++c) {
+      float ms = 0.f;
+      ok = cudaEventRecord(e0, p) == cudaSuccess && cudaGraphLaunch(exec[c], p) == cudaSuccess &&
+           cudaEventRecord(e1, p) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      t[c].push_back(ms);
+      g_tune_launches += kTuneCalls;
+    }
   int best = -1;
   float best_ms = INFINITY;
-  bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
-  const auto& L = registry(op);
-  for (size_t c = 0; ok && c < cand.size(); ++c) {
-    const Variant& v = L[cand[c]];
-    ok = v.launch(v, a, s) == LIFT_OK;                        // warm-up
-    float t[kTuneReps];
-    for (int r = 0; ok && r < kTuneReps; ++r) {
-      ok = cudaEventRecord(e0, s) == cudaSuccess && v.launch(v, a, s) == LIFT_OK &&
-           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-           cudaEventElapsedTime(&t[r], e0, e1) == cudaSuccess;
-    }
-    g_tune_launches += 1 + kTuneReps;
-    if (!ok) break;
-    std::sort(t, t + kTuneReps);
-    if (t[kTuneReps / 2] < best_ms) {
-      best_ms = t[kTuneReps / 2];
+  static const bool log = getenv("LIFT_TUNE_LOG") != nullptr;
+  for (size_t c = 0; ok && c < C; ++c) {
+    std::sort(t[c].begin(), t[c].end());
+    const float med = t[c][t[c].size() / 2];
+    if (log)
+      fprintf(stderr, "lift tune: op %d n %lld M %lld N %lld  %-36s %.4f ms per call\n", op,
+              (long long)(op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T ? a.M * a.N : a.n),
+              (long long)a.M, (long long)a.N, L[cand[c]].info.name, med / kTuneCalls);
+    if (med < best_ms) {
+      best_ms = med;
       best = cand[c];
     }
   }
+  if (p) cudaStreamSynchronize(p);
+  for (auto& x : exec)
+    if (x) cudaGraphExecDestroy(x);
+  if (ready) cudaEventDestroy(ready);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  if (scratch) {
-    cudaStreamSynchronize(s);
-    cudaFree(scratch);
-  }
+  if (p) cudaStreamDestroy(p);
+  if (scratch) cudaFree(scratch);
   if (!ok) {
     cudaGetLastError();
     return -1;
@@ -469,14 +531,26 @@ static int pick_variant(int op, const Args& a, cudaStream_t s = nullptr, bool ma
     const auto r = mlp_rank(op, a);
     if (!r.empty()) {
       v = r[0].second;
-      const TuneKey key{op, a.n, a.M, a.N, eligibility_bits(op, a)};
+      const bool matrix = op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T;   // shape = (M, N)
+      const TuneKey key{op, matrix ? 0 : a.n, a.M, a.N, eligibility_bits(op, a)};
       auto it = g_tuned.find(key);
       if (it != g_tuned.end()) {
         v = it->second;
-      } else if (may_tune && r.size() > 1 &&
-                 (!in_box(op, a) || r[1].first - r[0].first < kTuneMargin) && !capturing(s)) {
+      } else if (may_tune &&
+                 (!in_box(op, a) || (r.size() > 1 && r[1].first - r[0].first < kTuneMargin &&
+                                     input_bytes(op, a) >= 2.0 * l2_bytes())) &&
+                 !capturing(s)) {
         std::vector<int> cand;
-        for (size_t i = 0; i < r.size() && (int)i < kTuneTopK; ++i) cand.push_back(r[i].second);
+        auto add = [&](int c) {
+          if (c >= 0 && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+        };
+        for (size_t i = 0; i < r.size() && (int)i < kTuneTopK; ++i) add(r[i].second);
+        const auto& L = registry(op);
+        const int fixed = find_variant(op, kDefaultName[op]);
+        if (fixed >= 0 && eligible(op, L[fixed], a)) add(fixed);
+        const int known = (op + 1 < g_mlp.ops ? g_mlp.offsets[op + 1] : g_mlp.V) - g_mlp.offsets[op];
+        for (int i = known; i < (int)L.size(); ++i)      // newer than the model
+          if (eligible(op, L[i], a)) add(i);
         const int w = tune_candidates(op, a, cand, s);
         if (w >= 0) {
           g_tuned[key] = w;

@@ -100,8 +100,14 @@ def test_fallback_regret_beyond_the_trained_range(L):
     for op, n, M, N in shapes:
         policy_call, variant_call = _buffers(L, op, n, M, N)
         L.lift_set_policy(L.POLICY_FIXED)
-        times = {v: timer.per_call_ms([variant_call(v)], 5, 1)
-                 for v in range(L.lift_variant_count(op))}
+        # two passes over every variant (graphs of 4 back-to-back calls, 7
+        # replays each), the faster median of the two kept: the noise of one
+        # pass is about 1-2 %
+        times = {}
+        for _ in range(2):
+            for v in range(L.lift_variant_count(op)):
+                t = timer.per_call_ms([variant_call(v)] * 4, 7, 1)
+                times[v] = min(times.get(v, t), t)
         L.lift_set_policy(L.POLICY_MLP, costmodel.WEIGHTS)
         plain = L.lift_pick(op, n, M, N)
         L.lift_set_policy(L.POLICY_MLP_TUNE, costmodel.WEIGHTS)
@@ -117,5 +123,6 @@ def test_fallback_regret_beyond_the_trained_range(L):
     for r in rows:
         print("%-7s n=%d M=%d N=%d  plain %.4f  tuned %.4f" % r)
     print(f"geomean regret: plain learned pick {gm(4):.4f}, with the timing fallback {gm(5):.4f}")
-    assert gm(5) <= gm(4) + 1e-9
-    assert gm(5) <= 1.05
+    assert gm(5) < gm(4)
+    assert gm(5) <= 1.02
+    assert max(r[5] for r in rows) <= 1.05
