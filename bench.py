@@ -18,6 +18,15 @@ dot/scal workload on one GPU) also measures asum, both gemv shapes, mixed
 and batch after the headline step, each with its own roofline, oracle check
 and CPU baseline, under ``config.sub`` (``--no-sub`` skips them).
 
+Single-call workloads (asum_large, gemv, gemv-T, mixed, BlackScholes) submit
+their K timed steps as one CUDA graph replay (``--submit graph``, the
+default: the calls run back to back with no host launch between them, as a
+captured loop of calls runs); each kernel's duration comes from a graph of K
+launches of that call alone, timed with events on the replaying stream.  The
+same steps submitted one host call at a time (events around each call) are
+reported in ``config.eager``.  The dot/scal step is one launch of the
+library's own captured batch graph per step.
+
 Under torchrun each rank runs its own replica on its own GPU (the ops of
 one step do not exchange data); value is the bytes of all ranks divided by
 the slowest rank's time.
@@ -267,6 +276,9 @@ def run_ours(args, rank, world, dist):
     s = torch.cuda.current_stream()
     launches_per_step = 0
     kernels = []   # (tag, bytes per launch, start events, end events)
+    # (kernels entry, launch of that call) for workloads whose step is a few
+    # plain kernel calls: timed as CUDA graph replays (--submit graph)
+    graph_calls = []
     flushed = False  # True: an L2 flush runs between the timed spans of each step
     collect = None   # after the timed steps: the GPU results the oracle leg checks
 
@@ -407,6 +419,14 @@ def run_ours(args, rank, world, dist):
         bytes_step = sum(c[5] for c in calls)
         launches_per_step = 4
 
+        def mixed_call(i):
+            op, dt, da, v, name, nb = calls[i]
+            if len(da) == 2:
+                return lambda: lift.lift_asum_ex_v(v, dt, da[0], da[1], n, r[i:i + 1])
+            return lambda: lift.lift_dot_ex_v(v, dt, da[0], da[1], da[2], da[3], n, r[i:i + 1])
+
+        graph_calls = [(kernels[i], mixed_call(i)) for i in range(len(calls))]
+
         def step(timed):
             for i, (op, dt, da, v, name, nb) in enumerate(calls):
                 if timed:
@@ -437,6 +457,7 @@ def run_ours(args, rank, world, dist):
         bytes_step = 4 * n
         kas = ["asum:" + pa["name"], 4 * n, [], []]
         kernels = [kas]
+        graph_calls = [(kas, lambda: lift.lift_asum_v(va, x, n, r))]
 
         def step(timed):
             if timed:
@@ -497,6 +518,7 @@ def run_ours(args, rank, world, dist):
         bytes_step = 12 * n
         kb = ["blackscholes:" + pb["name"], bytes_step, [], []]
         kernels = [kb]
+        graph_calls = [(kb, lambda: lift.lift_blackscholes_v(vb, n, sp, *prm, call, put))]
 
         def step(timed):
             if timed:
@@ -656,6 +678,7 @@ def run_ours(args, rank, world, dist):
         bytes_step = 4 * M * N + 4 * nx + 8 * ny
         kg = [opname + ":" + pg["name"], bytes_step, [], []]
         kernels = [kg]
+        graph_calls = [(kg, lambda: call(vg, M, N, float(a), A, N, xv, float(b), yv))]
 
         def step(timed):
             if timed:
@@ -686,20 +709,53 @@ def run_ours(args, rank, world, dist):
         config = {"workload": WORKLOADS[wl]["desc"], "M": M, "N": N, "variants": [pg["name"]],
                   "l2": "no flush: A is 256 MiB, larger than the 129 MB L2"}
 
+    use_graph = bool(graph_calls) and args.submit == "graph" and not flushed
+    graphs = None
+    if use_graph:
+        # the K timed steps as one CUDA graph (calls back to back, as a loop
+        # of calls submits them once captured), and per call a graph of K
+        # launches of that call alone, which gives its average duration;
+        # captured before the timed region, each replayed once untimed
+        for _ in range(args.warmup):
+            step(False)
+        torch.cuda.synchronize()
+        graphs = {"step": torch.cuda.CUDAGraph()}
+        with torch.cuda.graph(graphs["step"]):
+            for _ in range(args.steps):
+                for _, fn in graph_calls:
+                    fn()
+        for i, (_, fn) in enumerate(graph_calls):
+            graphs[i] = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graphs[i]):
+                for _ in range(args.steps):
+                    fn()
+        for g in graphs.values():
+            g.replay()
+        torch.cuda.synchronize()
+        config["submitted_as"] = (f"CUDA graph of the {args.steps} timed steps (calls back to "
+                                  "back, no host launches); per-kernel time from a graph of "
+                                  f"{args.steps} launches of that call alone")
+
     # ---- clock sampler up first (its start-up idles the GPU), then the
     # warm-up steps right before the K timed steps, which are bracketed by
     # barrier + synchronize
     clocks = Clocks(local) if rank == 0 else None
     for _ in range(args.warmup):
-        step(False)
+        if use_graph:
+            graphs["step"].replay()
+        else:
+            step(False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(s)
-    for _ in range(args.steps):
-        step(True)
+    if use_graph:
+        graphs["step"].replay()
+    else:
+        for _ in range(args.steps):
+            step(True)
     t1.record(s)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
@@ -709,6 +765,16 @@ def run_ours(args, rank, world, dist):
         # of the per-step event spans, which bracket exactly the step's launches
         ms = sum(a.elapsed_time(b) for a, b in zip(kernels[0][2], kernels[0][3]))
         config["bracket_ms_including_flush"] = round(bracket_ms, 4)
+    if use_graph:
+        # per-call graphs: events on the stream that replays them
+        for i, (ke, _) in enumerate(graph_calls):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(s)
+            graphs[i].replay()
+            b_.record(s)
+            torch.cuda.synchronize()
+            per = a_.elapsed_time(b_) / args.steps
+            ke[2].append(per)
     clk = clocks.stop() if clocks else None
     ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
@@ -716,10 +782,34 @@ def run_ours(args, rank, world, dist):
 
     # ---- per-kernel durations (events on the launching stream)
     per_kernel = {}
-    for tag, kb, starts, ends in kernels:
-        d = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    for tag, nbytes, starts, ends in kernels:
+        if use_graph:
+            d = list(starts)             # durations per launch from the per-call graph
+        else:
+            d = [a.elapsed_time(b) for a, b in zip(starts, ends)]
         avg = sum(d) / len(d)
-        per_kernel[tag] = {"ms": avg, "gbs": kb / (avg / 1e3) / 1e9, "bytes": kb}
+        per_kernel[tag] = {"ms": avg, "gbs": nbytes / (avg / 1e3) / 1e9, "bytes": nbytes}
+    if use_graph:
+        # the same steps submitted one call at a time, with events around each
+        # call (context: the host launch path)
+        for ke in kernels:
+            ke[2].clear()
+            ke[3].clear()
+        for _ in range(3):
+            step(False)
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(s)
+        for _ in range(args.steps):
+            step(True)
+        e_b.record(s)
+        torch.cuda.synchronize()
+        config["eager"] = {
+            "value": round(job_rate(bytes_step, args.steps, 1, e_a.elapsed_time(e_b)), 1),
+            "kernels_gbs": {tag: round(nb / (sum(a.elapsed_time(b) for a, b in zip(st, en))
+                                             / len(st) / 1e3) / 1e9, 1)
+                            for tag, nb, st, en in kernels},
+            "submitted_as": "one host call per op per step, events around each call"}
+        graphs = None
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     peak, src = peaks()
     tr = traffic_for(dom.split(":", 1)[1])
@@ -1138,6 +1228,9 @@ def main():
     ap.add_argument("--variant", action="append",
                     help="force a variant by name (repeatable), e.g. for a profiling capture")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--submit", default="graph", choices=["graph", "eager"],
+                    help="single-call workloads: the timed steps as one CUDA graph replay "
+                         "(default) or as host calls with events around each")
     ap.add_argument("--no-sub", action="store_true",
                     help="dot_scal: skip the records of the other configurations")
     ap.add_argument("--no-extras", action="store_true",
