@@ -37,9 +37,9 @@
  *    TMA bulk copies (16 B) makes the library use the same variant family's
  *    guarded scalar-load form instead; it is not an error.
  *  - The reductions use a per-device workspace allocated by lift_init
- *    (partials, a ticket counter, a status word).  Reductions that run at
- *    the same time on different streams of one device share it and race:
- *    order them on one stream.
+ *    (partials, ticket counters, a status word), one slot per stream for up
+ *    to 8 streams of a device; calls on the same stream are ordered by it.
+ *    Calls on more than 8 streams at once share slots and can race.
  *  - lift_last_error() returns a detail message for the last failure of the
  *    calling thread.
  */
@@ -98,8 +98,20 @@ typedef enum {
  * ------------------------------------------------------------------------ */
 
 /* Set up `device`: query its SM count and allocate the reduction workspace
- * on it.  Must be called (once per device) before any other call on that
- * device, outside CUDA graph capture.  Calling it again is a no-op.
+ * on it: 8 slots of partials and tickets (about 17 MiB each), one per
+ * stream that launches work on the device (a stream takes the next slot on
+ * its first call; beyond 8 streams slots are shared in turn), so calls on
+ * up to 8 streams may run at the same time.  A CUDA graph keeps the slot of
+ * the stream it was captured on.  Must be called (once per device) before
+ * any other call on that device, outside CUDA graph capture.  Calling it
+ * again is a no-op.
+ * The first call also reads two environment overrides:
+ *   LIFT_POLICY  = fixed | table:<path> | mlp[:<path>] | mlp_tune[:<path>]
+ *                  (the learned policies default to the weights file
+ *                  data/mlp_gb300.txt beside the library);
+ *   LIFT_VARIANT = comma-separated variant names, each forced for its op.
+ * An unknown policy, an unreadable file or an unknown variant name makes
+ * this and every later lift_init return LIFT_ERR_INVALID_ARG.
  * Returns LIFT_ERR_CUDA / LIFT_ERR_NO_MEMORY on failure. */
 lift_status lift_init(int device);
 

@@ -1,5 +1,6 @@
 // C-ABI of liftblas (include/lift.h): device state, argument validation,
 // variant registry and policy, and the extern "C" entry points.
+#include <dlfcn.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -41,7 +42,8 @@ lift_status cuda_check(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 static std::mutex g_mu;
 static std::map<int, DeviceState*> g_states;
-constexpr int64_t kPartialCapacity = 1 << 22;   // fp32 partial slots (16 MiB)
+constexpr int64_t kPartialCapacity = 1 << 22;   // fp32 partial slots per workspace slot (16 MiB)
+constexpr int64_t kPartial64Capacity = 1 << 17; // FP64 partial slots per workspace slot (1 MiB)
 extern const int kTicketSlots = 64 + 65536;     // counters: reductions, then gemv-T column blocks
 
 DeviceState* current_state() {
@@ -50,6 +52,34 @@ DeviceState* current_state() {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_states.find(dev);
   return it == g_states.end() ? nullptr : it->second;
+}
+
+static Workspace& slot(DeviceState* st, int i) { return i == 0 ? st->ws : st->more[i - 1]; }
+
+// stream -> workspace slot, per device; a new stream takes the next slot
+static std::map<std::pair<DeviceState*, cudaStream_t>, int> g_slot_of;
+static std::map<DeviceState*, int> g_next_slot;
+
+Workspace* stream_workspace(DeviceState* st, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_pair(st, stream);
+  auto it = g_slot_of.find(key);
+  if (it == g_slot_of.end()) {
+    int& nx = g_next_slot[st];
+    it = g_slot_of.emplace(key, nx).first;
+    nx = (nx + 1) % kWsSlots;
+  }
+  return &slot(st, it->second);
+}
+
+static void free_slots(DeviceState* st) {
+  for (int i = 0; i < kWsSlots; ++i) {
+    Workspace& w = slot(st, i);
+    cudaFree(w.partials);
+    cudaFree(w.partials64);
+    cudaFree(w.tickets);
+    w = Workspace();
+  }
 }
 
 static lift_status init_device(int device) {
@@ -66,24 +96,26 @@ static lift_status init_device(int device) {
   st->device = device;
   rc = cuda_check(cudaDeviceGetAttribute(&st->sm_count, cudaDevAttrMultiProcessorCount, device),
                   "SM count");
-  if (rc == LIFT_OK)
-    rc = cuda_check(cudaMalloc(&st->ws.partials, kPartialCapacity * sizeof(float)), "workspace");
-  if (rc == LIFT_OK)
-    rc = cuda_check(cudaMalloc(&st->ws.partials64, 2 * kPartialCapacity * sizeof(double)),
-                    "workspace");
-  if (rc == LIFT_OK)
-    rc = cuda_check(cudaMalloc(&st->ws.tickets, kTicketSlots * sizeof(unsigned)), "workspace");
-  if (rc == LIFT_OK) rc = cuda_check(cudaMalloc(&st->ws.status, sizeof(int)), "workspace");
-  if (rc == LIFT_OK)
-    rc = cuda_check(cudaMemset(st->ws.tickets, 0, kTicketSlots * sizeof(unsigned)), "memset");
-  if (rc == LIFT_OK) rc = cuda_check(cudaMemset(st->ws.status, 0, sizeof(int)), "memset");
+  int* status = nullptr;
+  if (rc == LIFT_OK) rc = cuda_check(cudaMalloc(&status, sizeof(int)), "workspace");
+  if (rc == LIFT_OK) rc = cuda_check(cudaMemset(status, 0, sizeof(int)), "memset");
+  for (int i = 0; i < kWsSlots && rc == LIFT_OK; ++i) {
+    Workspace& w = slot(st, i);
+    rc = cuda_check(cudaMalloc(&w.partials, kPartialCapacity * sizeof(float)), "workspace");
+    if (rc == LIFT_OK)
+      rc = cuda_check(cudaMalloc(&w.partials64, kPartial64Capacity * sizeof(double)), "workspace");
+    if (rc == LIFT_OK)
+      rc = cuda_check(cudaMalloc(&w.tickets, kTicketSlots * sizeof(unsigned)), "workspace");
+    if (rc == LIFT_OK)
+      rc = cuda_check(cudaMemset(w.tickets, 0, kTicketSlots * sizeof(unsigned)), "memset");
+    w.status = status;
+    w.capacity = kPartialCapacity;
+    w.capacity64 = kPartial64Capacity;
+  }
   if (rc == LIFT_OK) rc = cuda_check(cudaDeviceSynchronize(), "init sync");
-  st->ws.capacity = kPartialCapacity;
   if (rc != LIFT_OK) {
-    cudaFree(st->ws.partials);
-    cudaFree(st->ws.partials64);
-    cudaFree(st->ws.tickets);
-    cudaFree(st->ws.status);
+    free_slots(st);
+    cudaFree(status);
     delete st;
     cudaSetDevice(prev);
     return rc;
@@ -455,7 +487,7 @@ static int tune_candidates(int op, const Args& a0, const std::vector<int>& cand,
     a.out = scratch;
     if (op == LIFT_OP_BLACKSCHOLES) a.result = scratch + a.n;
   } else {
-    a.result = st->ws.partials + (st->ws.capacity - 1);
+    a.result = a.ws->partials + (a.ws->capacity - 1);
     a.result64 = nullptr;
   }
   const auto& L = registry(op);
@@ -579,13 +611,16 @@ static lift_status resolve(int op, int variant, const Args& a, const Variant** o
   return LIFT_OK;
 }
 
-static lift_status run(int op, int variant, const Args& a, void* stream) {
+static lift_status run(int op, int variant, const Args& a0, void* stream) {
   DeviceState* st = current_state();
   if (!st) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Args a = a0;
+  a.ws = stream_workspace(st, s);
   const Variant* v = nullptr;
-  lift_status rc = resolve(op, variant, a, &v, static_cast<cudaStream_t>(stream), true);
+  lift_status rc = resolve(op, variant, a, &v, s, true);
   if (rc != LIFT_OK) return rc;
-  return v->launch(*v, a, static_cast<cudaStream_t>(stream));
+  return v->launch(*v, a, s);
 }
 
 static bool bad_n(int64_t n) { return n < 0; }
@@ -594,7 +629,74 @@ static bool bad_n(int64_t n) { return n < 0; }
 
 extern "C" {
 
-lift_status lift_init(int device) { return init_device(device); }
+// Environment overrides, read once, at the first lift_init:
+//   LIFT_POLICY  = fixed | table:<path> | mlp[:<path>] | mlp_tune[:<path>]
+//                  (without a path the learned policies read the weights file
+//                  that ships beside the library, data/mlp_gb300.txt)
+//   LIFT_VARIANT = comma-separated variant names, each forced for its op
+static std::string library_dir() {
+  Dl_info info;
+  if (!dladdr(reinterpret_cast<void*>(&lift_init), &info) || !info.dli_fname) return ".";
+  std::string f(info.dli_fname);
+  const size_t k = f.rfind('/');
+  return k == std::string::npos ? "." : f.substr(0, k);
+}
+
+static lift_status apply_env() {
+  const char* pol = getenv("LIFT_POLICY");
+  if (pol && *pol) {
+    std::string v(pol), kind = v, path;
+    const size_t c = v.find(':');
+    if (c != std::string::npos) {
+      kind = v.substr(0, c);
+      path = v.substr(c + 1);
+    }
+    int p = -1;
+    if (kind == "fixed") p = LIFT_POLICY_FIXED;
+    if (kind == "table") p = LIFT_POLICY_TABLE;
+    if (kind == "mlp") p = LIFT_POLICY_MLP;
+    if (kind == "mlp_tune") p = LIFT_POLICY_MLP_TUNE;
+    if (p < 0) return set_error(LIFT_ERR_INVALID_ARG, "LIFT_POLICY: unknown policy " + kind);
+    if (p == LIFT_POLICY_TABLE && path.empty())
+      return set_error(LIFT_ERR_INVALID_ARG, "LIFT_POLICY: table needs table:<path>");
+    if ((p == LIFT_POLICY_MLP || p == LIFT_POLICY_MLP_TUNE) && path.empty())
+      path = library_dir() + "/data/mlp_gb300.txt";
+    const lift_status rc = lift_set_policy(p, path.empty() ? nullptr : path.c_str());
+    if (rc != LIFT_OK) return set_error(rc, "LIFT_POLICY: " + g_last_error);
+  }
+  const char* var = getenv("LIFT_VARIANT");
+  if (var && *var) {
+    std::stringstream ss(var);
+    std::string name;
+    while (std::getline(ss, name, ',')) {
+      if (name.empty()) continue;
+      int found = -1;
+      for (int op = 0; op < LIFT_NUM_OPS && found < 0; ++op) {
+        const auto& L = registry(op);
+        for (size_t i = 0; i < L.size(); ++i)
+          if (name == L[i].info.name) {
+            found = op;
+            lift_set_variant(op, (int)i);
+            break;
+          }
+      }
+      if (found < 0) return set_error(LIFT_ERR_INVALID_ARG, "LIFT_VARIANT: unknown variant " + name);
+    }
+  }
+  return LIFT_OK;
+}
+
+lift_status lift_init(int device) {
+  static std::once_flag once;
+  static lift_status env_rc = LIFT_OK;
+  static std::string env_msg;
+  std::call_once(once, [] {
+    env_rc = apply_env();
+    if (env_rc != LIFT_OK) env_msg = g_last_error;
+  });
+  if (env_rc != LIFT_OK) return set_error(env_rc, env_msg);
+  return init_device(device);
+}
 
 lift_status lift_finalize(void) {
   noalloc_forget();
@@ -604,13 +706,14 @@ lift_status lift_finalize(void) {
   for (auto& kv : g_states) {
     cudaSetDevice(kv.first);
     cudaDeviceSynchronize();
-    cudaFree(kv.second->ws.partials);
-    cudaFree(kv.second->ws.partials64);
-    cudaFree(kv.second->ws.tickets);
-    cudaFree(kv.second->ws.status);
+    int* status = kv.second->ws.status;
+    free_slots(kv.second);
+    cudaFree(status);
     delete kv.second;
   }
   g_states.clear();
+  g_slot_of.clear();
+  g_next_slot.clear();
   if (prev >= 0) cudaSetDevice(prev);
   return LIFT_OK;
 }
@@ -646,11 +749,12 @@ int lift_read_status(int clear) {
     // after a recorded failure, also return every "last CTA" ticket to 0
     // (a kernel that gave up still takes its ticket, so they should be; this
     // restores them whatever path the failure took).  Waits for the device.
-    if (cudaDeviceSynchronize() != cudaSuccess ||
-        cudaMemset(st->ws.tickets, 0, kTicketSlots * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(st->ws.status, 0, sizeof(int)) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess)
-      return LIFT_ERR_CUDA;
+    bool ok = cudaDeviceSynchronize() == cudaSuccess;
+    for (int i = 0; i < kWsSlots && ok; ++i)
+      ok = cudaMemset(slot(st, i).tickets, 0, kTicketSlots * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && cudaMemset(st->ws.status, 0, sizeof(int)) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) return LIFT_ERR_CUDA;
   }
   return v;
 }
@@ -675,14 +779,16 @@ lift_status lift_asum_v(int variant, const float* x, int64_t n, float* result, d
 
 // The fp32 result of a shard call goes to the last fp32 workspace slot (no
 // kernel uses it: grids and partial counts stay below the capacity).
-static float* shard_discard() {
+static float* shard_discard(void* stream) {
   DeviceState* st = current_state();
-  return st ? st->ws.partials + (st->ws.capacity - 1) : nullptr;
+  if (!st) return nullptr;
+  Workspace* w = stream_workspace(st, static_cast<cudaStream_t>(stream));
+  return w->partials + (w->capacity - 1);
 }
 
 lift_status lift_asum_partial(const float* x, int64_t n, double* partial, void* stream) {
   if (!partial) return set_error(LIFT_ERR_INVALID_ARG, "asum_partial: partial is NULL");
-  float* r = shard_discard();
+  float* r = shard_discard(stream);
   if (!r) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
   return lift_asum_v(-1, x, n, r, partial, stream);
 }
@@ -690,7 +796,7 @@ lift_status lift_asum_partial(const float* x, int64_t n, double* partial, void* 
 lift_status lift_dot_partial(const float* x, const float* y, int64_t n, double* partial,
                              void* stream) {
   if (!partial) return set_error(LIFT_ERR_INVALID_ARG, "dot_partial: partial is NULL");
-  float* r = shard_discard();
+  float* r = shard_discard(stream);
   if (!r) return set_error(LIFT_ERR_NOT_INITIALIZED, "lift_init was not called for this device");
   return lift_dot_v(-1, x, y, n, r, partial, stream);
 }

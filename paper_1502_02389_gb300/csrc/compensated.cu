@@ -116,8 +116,9 @@ struct CompReduce {
     const float* x = static_cast<const float*>(a.x);
     const float* y = static_cast<const float*>(a.y);
     int64_t n = a.n;
-    double* partials = st->ws.partials64;
-    unsigned* ticket = st->ws.tickets + kCompTicket;
+    if (g > st->ws.capacity64) return set_error(LIFT_ERR_UNSUPPORTED, "grid exceeds workspace");
+    double* partials = a.ws->partials64;
+    unsigned* ticket = a.ws->tickets + kCompTicket;
     float* result = a.result;
     double* result64 = a.result64;
     void* args[] = {&x, &y, &n, &partials, &ticket, &result, &result64};

@@ -141,7 +141,7 @@ struct GemvSplit {
     const float* A = a.A;
     const float* x = static_cast<const float*>(a.x);
     float* y = a.out;
-    float* partials = st->ws.partials;
+    float* partials = a.ws->partials;
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &L, &S, &partials};
     lift_status r = launch_config(kernel(), dim3((unsigned)(M * S)), dim3(THREADS), 0, 1, s, args);
     if (r != LIFT_OK || S == 1) return r;

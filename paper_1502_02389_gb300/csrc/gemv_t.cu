@@ -286,8 +286,8 @@ struct GemvT {
     const float* A = a.A;
     const float* x = static_cast<const float*>(a.x);
     float* y = a.out;
-    float* partials = st->ws.partials;
-    unsigned* tickets = st->ws.tickets + kTicketBase;
+    float* partials = a.ws->partials;
+    unsigned* tickets = a.ws->tickets + kTicketBase;
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
     lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
     if (r != LIFT_OK || PASSES == 1) return r;
@@ -338,8 +338,8 @@ struct GemvTCluster {
     const float* A = a.A;
     const float* x = static_cast<const float*>(a.x);
     float* y = a.out;
-    float* partials = st->ws.partials;
-    unsigned* tickets = st->ws.tickets + kTicketBase;
+    float* partials = a.ws->partials;
+    unsigned* tickets = a.ws->tickets + kTicketBase;
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ncb, (unsigned)RB);

@@ -25,17 +25,27 @@ struct Workspace {
   float* partials = nullptr;       // per-CTA fp32 partial sums
   double* partials64 = nullptr;    // per-CTA FP64 partials (sum, compensation pairs)
   unsigned* tickets = nullptr;     // one-pass "last CTA" counters (kept at 0 between calls)
-  int* status = nullptr;           // device status word (0 = ok, else lift_status)
-  int64_t capacity = 0;            // partial slots
+  int* status = nullptr;           // device status word (0 = ok, else lift_status), shared
+  int64_t capacity = 0;            // fp32 partial slots
+  int64_t capacity64 = 0;          // FP64 partial slots
 };
+
+// Workspace slots per device: each stream that launches work gets its own
+// slot (round robin once there are more streams than slots), so reductions
+// running at the same time on different streams do not share partials or
+// tickets.
+constexpr int kWsSlots = 8;
 
 struct DeviceState {
   int device = -1;
   int sm_count = 0;
-  Workspace ws;
+  Workspace ws;                    // slot 0 (also the capacities and the status word)
+  Workspace more[kWsSlots - 1];    // slots 1 ..
 };
 
 DeviceState* current_state();  // state of the current device, or nullptr
+// The workspace slot of `stream` on the current device (assigned on first use).
+Workspace* stream_workspace(DeviceState* st, cudaStream_t stream);
 void noalloc_forget();          // drop lift_asum_noalloc's cached per-device addresses
 
 lift_status set_error(lift_status s, const std::string& msg);
@@ -56,6 +66,7 @@ struct Args {
   float* out = nullptr;            // scal / gemv output vector
   float* result = nullptr;         // reduction result
   double* result64 = nullptr;
+  Workspace* ws = nullptr;         // the calling stream's workspace slot (set by the entry point)
   int64_t n = 0, M = 0, N = 0, lda = 0;
   float alpha = 0.f, beta = 0.f;
 };

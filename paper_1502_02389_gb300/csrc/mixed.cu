@@ -283,8 +283,9 @@ struct Mixed {
     const float* xs = a.xscale;
     const float* ys = a.yscale;
     int64_t n = a.n;
-    double* partials = st->ws.partials64;
-    unsigned* ticket = st->ws.tickets + 1;
+    if (g > st->ws.capacity64) return set_error(LIFT_ERR_UNSUPPORTED, "grid exceeds workspace");
+    double* partials = a.ws->partials64;
+    unsigned* ticket = a.ws->tickets + 1;
     float* result = a.result;
     double* result64 = a.result64;
     void* args[] = {&x, &xs, &y, &ys, &n, &partials, &ticket, &result, &result64};

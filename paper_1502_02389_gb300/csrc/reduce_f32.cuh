@@ -340,8 +340,8 @@ struct ReduceF32 {
     const float* x = static_cast<const float*>(a.x);
     const float* y = static_cast<const float*>(a.y);
     int64_t n = a.n;
-    float* partials = st->ws.partials;
-    unsigned* ticket = st->ws.tickets;
+    float* partials = a.ws->partials;
+    unsigned* ticket = a.ws->tickets;
     float* result = a.result;
     double* result64 = a.result64;
     int* status = st->ws.status;
