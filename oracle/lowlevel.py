@@ -16,11 +16,11 @@ from __future__ import annotations
 
 import math
 
-from .patterns import (AsScalar, AsVector, C, Id, Iterate, Join, Map, MapLocal,
-                       MapSeq, MapWorkgroup, PadTo, PartRed, Reduce, ReduceSeq,
-                       Reorder, ReorderStride, Split, ToGlobal, ToLocal, Vect, Zip,
-                       ZipWith, abs_, absAndPlus, add, add64, fold, id_, mul3,
-                       mult, mult_by, sqrt64, square, to_f32, to_f64)
+from .patterns import (AsScalar, AsVector, C, Id, Iterate, Join, Map, MapLocal, MapSeq,
+                       MapWorkgroup, PadTo, PartRed, Reduce, ReduceSeq, ReduceSeqComp, Reorder,
+                       ReorderStride, Split, ToGlobal, ToLocal, Vect, Zip, ZipWith, abs_,
+                       absAndPlus, add, add64, fold, id_, mul3, mult, mult_by, sqrt64, square,
+                       to_f32, to_f64)
 
 # the fused reduction function of each reduce program (rule 3f applied to
 # reduce(add, 0) . map(g)); sum has no map and folds add itself
@@ -145,16 +145,21 @@ def final_combine(P: int, ft: int, cast32: bool = True, post=None):
 
 def cta_expr(op: str, K: int, tile: int, vw: int, threads: int, stride: bool = True):
     """One CTA folding K tiles of ``tile`` elements (in order) into one
-    value: per-thread folds over vect^vw lanes, lane sum, block tree."""
+    value: every thread folds its J vectors of each tile from zero (over
+    vect^vw lanes) and adds the tile's lanes in order, adds its K tile
+    values with the compensated reduce-seq (the partial reduction of Fig. 3d
+    applied to the thread's reduce-seq, its outer level compensated), then
+    the block tree."""
     V = tile // vw
     J = V // threads
     assert V % threads == 0 and tile % vw == 0
     f = FOLD[op]
     fr = Vect(vw, f) if vw > 1 else f
-    lanes = Id()
-    if vw > 1:
-        lanes = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
-    return C(block_tree(threads), lanes, Join(), MapLocal(ReduceSeq(fr, 0)),
+    tile_value = ReduceSeq(fr, 0)
+    if vw > 1:          # the tile's lane sums added in order
+        tile_value = C(ReduceSeq(add, 0), AsScalar(), ReduceSeq(fr, 0))
+    per_thread = C(ReduceSeqComp(add), Join(), Map(tile_value), Split(J))
+    return C(block_tree(threads), Join(), MapLocal(per_thread),
              _thread_order(threads, K * J, J, stride),
              AsVector(vw) if vw > 1 else Id())
 
@@ -208,19 +213,34 @@ def reduce_variant(op: str, n: int, tile: int, vw: int, threads: int, grid: int,
     return e, L
 
 
+GEMV_GROUP = 8   # vectors a gemv lane folds plainly before a compensated add
+
+
+def grouped_dot(vw: int, J: int, group: int = GEMV_GROUP):
+    """[J] zipped vectors of one lane -> [1]: groups of ``group``
+    consecutive vectors (the last padded with zeros), each folded from zero
+    over the vw lanes with its lanes then added in order, and the group
+    values added with the compensated reduce-seq (the partial reduction of
+    Fig. 3d applied to the lane's reduce-seq, its outer level
+    compensated)."""
+    f = fold(add, mult)
+    fr = Vect(vw, f) if vw > 1 else f
+    value = ReduceSeq(fr, 0)
+    if vw > 1:
+        value = C(ReduceSeq(add, 0), AsScalar(), ReduceSeq(fr, 0))
+    Jp = max(group, math.ceil(J / group) * group)
+    return C(ReduceSeqComp(add), Join(), Map(value), Split(group), PadTo(Jp))
+
+
 def gemv_row_variant(N: int, vw: int, lanes: int = WARP):
     """Expression of one row of the gemv kernel: ``lanes`` threads share the
-    row; lane l folds vectors l, l+lanes, ... of the zero-padded row
-    (zipped with x) in order, adds its vector lanes, then ``block_tree``."""
+    row; lane l takes vectors l, l+lanes, ... of the zero-padded row
+    (zipped with x) in order and folds them with ``grouped_dot``, then
+    ``block_tree``."""
     chunk = lanes * vw
     Np = max(chunk, math.ceil(N / chunk) * chunk)
     J = Np // chunk
-    f = fold(add, mult)
-    fr = Vect(vw, f) if vw > 1 else f
-    lane_sum = Id()
-    if vw > 1:
-        lane_sum = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
-    return C(block_tree(lanes), lane_sum, Join(), MapLocal(ReduceSeq(fr, 0)),
+    return C(block_tree(lanes), Join(), MapLocal(grouped_dot(vw, J)),
              Split(J), ReorderStride(s=lanes),
              AsVector(vw) if vw > 1 else Id(), PadTo(Np), ZipWith("x"))
 
@@ -237,23 +257,19 @@ def gemv_z_variant(M: int, N: int, alpha, vw: int, lanes: int = WARP,
 def gemv_split_z_variant(M: int, N: int, alpha, vw: int, threads: int, L: int, S: int):
     """z of the split-row gemv: each row zipped with x, padded to S*L and
     split into S segments of L elements; a CTA of ``threads`` folds a
-    segment (thread t takes vectors t, t+threads, ... in order, adds its vw
-    lanes, then ``block_tree``); the S segment partials of the row are added
-    by one warp (lane l takes partials l, l+32, ..., then a halving tree)
-    and multiplied by alpha -- the partial-reduction rule of Fig. 3 applied
-    to each row's reduce."""
+    segment (thread t takes vectors t, t+threads, ... in order and folds
+    them with ``grouped_dot``, then ``block_tree``); the S segment partials
+    of the row are added by one warp (lane l adds partials l, l+32, ...
+    with the compensated reduce-seq, then a halving tree) and multiplied by
+    alpha -- the partial-reduction rule of Fig. 3 applied to each row's
+    reduce."""
     chunk = threads * vw
     assert L % chunk == 0 and S * L >= N
     J = L // chunk
-    f = fold(add, mult)
-    fr = Vect(vw, f) if vw > 1 else f
-    lane_sum = Id()
-    if vw > 1:
-        lane_sum = C(Join(), MapLocal(ReduceSeq(add, 0)), Split(vw), AsScalar())
-    segment = C(block_tree(threads), lane_sum, Join(), MapLocal(ReduceSeq(fr, 0)),
+    segment = C(block_tree(threads), Join(), MapLocal(grouped_dot(vw, J)),
                 Split(J), ReorderStride(s=threads), AsVector(vw) if vw > 1 else Id())
     per = max(1, math.ceil(S / WARP))
-    lanes = C(halving_tree(add), Join(), MapLocal(ReduceSeq(add, 0)), Split(per),
+    lanes = C(halving_tree(add), Join(), MapLocal(ReduceSeqComp(add)), Split(per),
               ReorderStride(s=WARP), PadTo(WARP * per))
     row = C(Join(), MapWorkgroup(lanes), Split(S), Join(), MapWorkgroup(segment), Split(L),
             PadTo(S * L), ZipWith("x"))
@@ -261,26 +277,30 @@ def gemv_split_z_variant(M: int, N: int, alpha, vw: int, threads: int, L: int, S
 
 
 def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int, passes: int = 1,
-                     cluster: int = 1):
+                     cluster: int = 1, group: int = 16):
     """z of the gemv-T kernel: every column of A (the rows of the
     reorder-stride view) zipped with x, padded to RB*B, folded in RB blocks
-    of B rows (fp32); the block partials are then combined in fp32 --
-    one pass: added in block order; one pass with clusters of ``cluster``
-    blocks: each cluster's consecutive block partials added in order, then
-    the cluster sums added in order (the partial reduction of Fig. 3d
-    applied to the block partials); two pass: lane l of one warp adds
-    partials l, l+32, ..., then a halving tree over the lanes -- and
-    multiplied by alpha."""
+    of B rows (fp32; a block's rows in groups of ``group``, each group
+    folded from zero, the group sums added with the compensated reduce-seq);
+    the block partials are then combined in fp32 --
+    one pass: added in block order with the compensated reduce-seq; one pass
+    with clusters of ``cluster`` blocks: each cluster's consecutive block
+    partials added in order, then the cluster sums added in order with the
+    compensated reduce-seq (the partial reduction of Fig. 3d applied to the
+    block partials); two pass: lane l of one warp adds partials l, l+32,
+    ..., then a halving tree over the lanes -- and multiplied by alpha."""
     if passes == 1 and cluster > 1:
         assert RB % cluster == 0
-        combine = C(ReduceSeq(add, 0), Join(), Map(ReduceSeq(add, 0)), Split(cluster))
+        combine = C(ReduceSeqComp(add), Join(), Map(ReduceSeq(add, 0)), Split(cluster))
     elif passes == 1:
-        combine = ReduceSeq(add, 0)
+        combine = ReduceSeqComp(add)
     else:
         per = max(1, math.ceil(RB / WARP))
-        lanes = C(halving_tree(add), Join(), MapLocal(ReduceSeq(add, 0)), Split(per),
+        lanes = C(halving_tree(add), Join(), MapLocal(ReduceSeqComp(add)), Split(per),
                   ReorderStride(s=WARP), PadTo(WARP * per))
         combine = C(Join(), MapWorkgroup(lanes), Split(RB))     # one warp per column
-    col = C(combine, Join(),
-            Map(ReduceSeq(fold(add, mult), 0)), Split(B), PadTo(RB * B), ZipWith("x"))
+    Bp = math.ceil(B / group) * group
+    block = C(ReduceSeqComp(add), Join(), Map(ReduceSeq(fold(add, mult), 0)), Split(group),
+              PadTo(Bp))
+    col = C(combine, Join(), Map(block), Split(B), PadTo(RB * B), ZipWith("x"))
     return C(Map(mult_by(alpha)), Join(), Map(col), Split(M), ReorderStride(s=N), Join())

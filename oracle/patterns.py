@@ -193,6 +193,17 @@ def PartRed(f, z=0):
     return Reduce(f, z, "part-red")
 
 
+def ReduceSeqComp(f=None):
+    """reduce-seq with a (sum, compensation) accumulator: Neumaier's
+    compensated summation (Neumaier 1974).  For each element t in order:
+    s' = s + t; c = c + ((s - s') + t if |s| >= |t| else (t - s') + s);
+    s = s'; the result is s + c (s itself when s is not finite, so an Inf
+    among the terms stays Inf).  In exact arithmetic this is reduce(add, 0);
+    in fp32 its error is about 2u|sum| whatever the number of elements.
+    ``f`` is add, or vect^n(add) to sum vectors lane by lane."""
+    return Reduce(add if f is None else f, 0, "reduce-seq-comp")
+
+
 @dataclass(frozen=True)
 class Zip(Expr):
     """zip(a, b): consumes a 2-tuple of equal-length arrays (Table 1)."""
@@ -657,6 +668,31 @@ def _fold_axis(ar: _Arith, f, z, v, ax: int):
     return acc
 
 
+def _comp_fold_axis(v, ax: int):
+    """Neumaier-compensated left fold of ``v`` along axis ``ax`` (see
+    ReduceSeqComp), every operation in the mode's arithmetic (numpy float32
+    arithmetic rounds each operation to nearest, as the kernels' explicit
+    fp32 operations do)."""
+    if isinstance(v, Pair):
+        raise PatternTypeError("compensated reduction over pairs")
+    d = np.asarray(v.data)
+    shape = list(d.shape)
+    m = shape[ax]
+    del shape[ax]
+    s = np.zeros(shape, dtype=d.dtype)
+    c = np.zeros(shape, dtype=d.dtype)
+    with np.errstate(invalid="ignore", over="ignore"):
+        for i in range(m):
+            t = np.take(d, i, axis=ax)
+            u = s + t
+            big = np.abs(s) >= np.abs(t)
+            c = c + np.where(big, (s - u) + t, (t - u) + s)
+            s = u
+        if d.dtype.kind == "f":
+            return np.where(np.isfinite(s), s + c, s)
+    return s + c
+
+
 # ---------------------------------------------------------------------------
 # evaluation
 # ---------------------------------------------------------------------------
@@ -680,7 +716,10 @@ def _eval(e, v, nb: int, ar: _Arith, env: Dict[str, np.ndarray]):
             return Arr(np.asarray(ar.apply(e.f, v.data)), v.vw)
         return _eval(e.f, v, nb + 1, ar, env)
     if isinstance(e, Reduce):
-        acc = _fold_axis(ar, e.f, e.z, v, nb)
+        if e.kind == "reduce-seq-comp":
+            acc = _comp_fold_axis(v, nb)
+        else:
+            acc = _fold_axis(ar, e.f, e.z, v, nb)
         return Arr(np.expand_dims(np.asarray(acc), nb), v.vw)
     if isinstance(e, Split):
         def sp(d):

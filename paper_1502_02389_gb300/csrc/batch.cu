@@ -6,8 +6,10 @@
 // handed out by an atomic queue head (largest items first, so the tail of
 // the launch is made of small items).  A CTA processes an item exactly as
 // the standalone kernels process their tiles (the item's tiles in order,
-// thread t folding vectors t + THREADS*j of each tile, lane sum, block
-// tree); for asum / dot each item leaves one fp32 partial, and the CTA that
+// thread t folding vectors t + THREADS*j of each tile, adding the tile's
+// lanes, and adding the tile values with Neumaier's compensated step, then
+// the block tree); for asum / dot
+// each item leaves one fp32 partial, and the CTA that
 // finishes an op's last item (an atomic per-op counter) adds that op's item
 // partials in item order in FP64 (thread t takes partials t, t+256, ...,
 // then an FP64 block tree) and writes the rounded result.  Nothing waits:
@@ -83,9 +85,7 @@ template <int OP, int VW, int J>
 __device__ float reduce_item(const OpDev& o, int64_t begin, int64_t end, float* red) {
   constexpr int64_t TILE = (int64_t)kThreads * VW * J;
   const int t = threadIdx.x;
-  float acc[VW];
-#pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = 0.f;
+  float acc = 0.f, cmp = 0.f;  // sum of the tile values and its Neumaier compensation
   int64_t base = begin;
   for (; base + TILE <= end; base += TILE) {
     Vec<VW> a[J], b[J];
@@ -95,23 +95,34 @@ __device__ float reduce_item(const OpDev& o, int64_t begin, int64_t end, float* 
       ld_stream(o.x + e, a[j]);
       if constexpr (OP == LIFT_OP_DOT) ld_stream(o.y + e, b[j]);
     }
+    float ts[VW];
 #pragma unroll
-    for (int j = 0; j < J; ++j) fold<OP, VW>(acc, a[j], b[j]);
+    for (int l = 0; l < VW; ++l) ts[l] = 0.f;
+#pragma unroll
+    for (int j = 0; j < J; ++j) fold<OP, VW>(ts, a[j], b[j]);
+    float tv = ts[0];
+#pragma unroll
+    for (int l = 1; l < VW; ++l) tv = __fadd_rn(tv, ts[l]);
+    neumaier_add(acc, cmp, tv);
   }
   if (base < end) {
+    float ts[VW];
+#pragma unroll
+    for (int l = 0; l < VW; ++l) ts[l] = 0.f;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       const int64_t e = base + (int64_t)(t + kThreads * j) * VW;
       Vec<VW> a, b;
       ld_guarded<VW>(o.x, e, end, a);
       if constexpr (OP == LIFT_OP_DOT) ld_guarded<VW>(o.y, e, end, b);
-      fold<OP, VW>(acc, a, b);
+      fold<OP, VW>(ts, a, b);
     }
-  }
-  float r = acc[0];
+    float tv = ts[0];
 #pragma unroll
-  for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
-  return block_tree<kThreads>(r, red);
+    for (int l = 1; l < VW; ++l) tv = __fadd_rn(tv, ts[l]);
+    neumaier_add(acc, cmp, tv);
+  }
+  return block_tree<kThreads>(neumaier_value(acc, cmp), red);
 }
 
 template <int VW, int J>
@@ -155,12 +166,12 @@ __device__ void gemv_item(const OpDev& o, int64_t r0, int64_t r1) {
   constexpr int U = VW == 1 ? 8 : (VW == 4 ? 4 : 2);
   const int lane = threadIdx.x & (kWarp - 1);
   const int64_t chunks = o.N / kChunk;
+  static_assert(kGemvGroup % U == 0, "an unrolled step stays inside one group");
   for (int64_t row = r0 + threadIdx.x / kWarp; row < r1; row += kThreads / kWarp) {
     const float* a = o.A + row * o.lda;
-    float acc[VW];
-#pragma unroll
-    for (int l = 0; l < VW; ++l) acc[l] = 0.f;
-    int64_t c = 0;
+    GroupedDot<VW> acc;
+    acc.init();
+    int64_t c = 0;                     // the lane's vector index along the row
     for (; c + U <= chunks; c += U) {
       Vec<VW> va[U], vx[U];
 #pragma unroll
@@ -170,26 +181,25 @@ __device__ void gemv_item(const OpDev& o, int64_t r0, int64_t r1) {
         ld_x<VW>(o.x + e, vx[u]);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) fold<LIFT_OP_DOT, VW>(acc, va[u], vx[u]);
+      for (int u = 0; u < U; ++u) acc.add(va[u], vx[u]);
+      if ((c + U) % kGemvGroup == 0) acc.flush();
     }
     for (; c < chunks; ++c) {
       Vec<VW> va, vx;
       const int64_t e = c * kChunk + lane * VW;
       ld_stream(a + e, va);
       ld_x<VW>(o.x + e, vx);
-      fold<LIFT_OP_DOT, VW>(acc, va, vx);
+      acc.add(va, vx);
+      if ((c + 1) % kGemvGroup == 0) acc.flush();
     }
     if (chunks * kChunk < o.N) {
       Vec<VW> va, vx;
       const int64_t e = chunks * kChunk + lane * VW;
       ld_guarded<VW>(a, e, o.N, va);
       ld_guarded<VW>(o.x, e, o.N, vx);
-      fold<LIFT_OP_DOT, VW>(acc, va, vx);
+      acc.add(va, vx);
     }
-    float r = acc[0];
-#pragma unroll
-    for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
-    r = warp_tree(r);
+    float r = warp_tree(acc.value());
     if (lane == 0) {
       const float z = __fmul_rn(o.alpha, r);
       o.out[row] = o.beta == 0.f ? z : __fadd_rn(z, __fmul_rn(o.beta, o.out[row]));

@@ -47,12 +47,6 @@ __device__ __forceinline__ void ld_x_vec(const float* p, Vec<VW>& o) {
   }
 }
 
-template <int VW>
-__device__ __forceinline__ void fold_pair(float (&acc)[VW], const Vec<VW>& a, const Vec<VW>& b) {
-#pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a.v[l], b.v[l]));
-}
-
 template <int THREADS, int VW, int U>
 __global__ void __launch_bounds__(THREADS)
     gemv_split(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
@@ -62,12 +56,13 @@ __global__ void __launch_bounds__(THREADS)
   __shared__ float red[kWarp];
   const int64_t r = blockIdx.x / S, seg = blockIdx.x % S;
   const int64_t c_end = (seg + 1) * L < N ? (seg + 1) * L : N;
+  static_assert(kGemvGroup % U == 0, "an unrolled step stays inside one group");
   const float* row = A + r * lda;
-  float acc[VW];
-#pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = 0.f;
+  GroupedDot<VW> acc;
+  acc.init();
+  int64_t k = 0;             // the thread's vector index within the segment
   int64_t c = seg * L + (int64_t)threadIdx.x * VW;
-  for (; c + (U - 1) * kStep + VW <= c_end; c += U * kStep) {
+  for (; c + (U - 1) * kStep + VW <= c_end; c += U * kStep, k += U) {
     Vec<VW> a[U], b[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -75,24 +70,23 @@ __global__ void __launch_bounds__(THREADS)
       ld_x_vec<VW>(x + c + u * kStep, b[u]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) fold_pair<VW>(acc, a[u], b[u]);
+    for (int u = 0; u < U; ++u) acc.add(a[u], b[u]);
+    if ((k + U) % kGemvGroup == 0) acc.flush();
   }
-  for (; c + VW <= c_end; c += kStep) {
+  for (; c + VW <= c_end; c += kStep, ++k) {
     Vec<VW> a, b;
     ld_stream(row + c, a);
     ld_x_vec<VW>(x + c, b);
-    fold_pair<VW>(acc, a, b);
+    acc.add(a, b);
+    if ((k + 1) % kGemvGroup == 0) acc.flush();
   }
   if (c < c_end) {           // the ragged last vector of the row
     Vec<VW> a, b;
     ld_guarded<VW>(row, c, c_end, a);
     ld_guarded<VW>(x, c, c_end, b);
-    fold_pair<VW>(acc, a, b);
+    acc.add(a, b);
   }
-  float d = acc[0];
-#pragma unroll
-  for (int l = 1; l < VW; ++l) d = __fadd_rn(d, acc[l]);
-  d = block_tree<THREADS>(d, red);
+  float d = block_tree<THREADS>(acc.value(), red);
   if (S > 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x != 0) return;
   if (S > 1) {

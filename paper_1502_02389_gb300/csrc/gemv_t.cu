@@ -7,17 +7,21 @@
 // matrix:  z_j = alpha * dot(col_j, x),  y'_j = z_j + beta * y_j.
 // The kernels evaluate, per column j,
 //
-//   map(mult(alpha)) . map(to_f32) . COMBINE . map(to_f64) . join
-//     . map(reduce-seq(lambda acc,(a,b): acc + a*b, 0)) . split^B
-//     . pad-(RB*B) . zip(col_j, x)
+//   map(mult(alpha)) . COMBINE . join . map(BLOCK) . split^B . pad-(RB*B)
+//     . zip(col_j, x)
+//   BLOCK = reduce-seq-comp . join . map(reduce-seq(lambda acc,(a,b):
+//             acc + a*b, 0)) . split^16 . pad
+// (reduce-seq-comp: Neumaier's compensated reduce-seq)
 //
 // i.e. the column is split into RB uniform blocks of B rows (the last one
-// padded with zeros); CTA (cb, rb) folds the rows of block rb in order for
+// padded with zeros); CTA (cb, rb) folds the rows of block rb -- in groups
+// of 16 rows folded in order, the group sums added with Neumaier's
+// compensated step -- for
 // its THREADS*VW consecutive columns (thread t owns VW adjacent columns, so
 // a warp reads 32*VW*4 contiguous bytes of every row) and writes one fp32
 // partial per column.  The two lowerings of COMBINE are a rewrite choice:
-//   one pass:  reduce-seq(add) over the RB partials in block order, done by
-//              the last CTA of each column block (an atomic ticket per
+//   one pass:  reduce-seq-comp over the RB partials in block order, done
+//              by the last CTA of each column block (an atomic ticket per
 //              column block); row-major partials P[rb][j];
 //   two pass:  a second kernel, one warp per column: lane l folds partials
 //              l, l+32, ... , then a halving tree over the 32 lanes;
@@ -46,45 +50,63 @@ lift_status launch_rows_combine(int64_t n, int64_t per, float alpha, float beta,
 
 namespace {
 
-// Row block [r0, r1) of this thread's VW columns c0 .. c0+VW-1, folded in
-// row order into acc (fp32; zero for an empty block).
+// Rows folded plainly before a compensated add (see fold_rows).
+constexpr int kGroupRows = 16;
+
+// Row block [r0, r1) of this thread's VW columns c0 .. c0+VW-1 (zero for an
+// empty block): the rows in groups of kGroupRows, each group's products
+// folded in row order from zero (U rows of loads in flight at a time), and
+// the group sums added with Neumaier's compensated step (the partial
+// reduction of Fig. 3d within the block's reduce-seq), so the error of a
+// column's block value does not grow with the block length.
 template <int VW, int U>
 __device__ __forceinline__ void fold_rows(int64_t N, const float* __restrict__ A, int64_t lda,
                                           const float* __restrict__ x, int64_t c0, int64_t r0,
                                           int64_t r1, float* acc) {
+  static_assert(kGroupRows % U == 0, "a group holds whole unrolled steps");
+  float cmp[VW];
 #pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = 0.f;
+  for (int l = 0; l < VW; ++l) acc[l] = cmp[l] = 0.f;
   const bool full_cols = c0 + VW <= N;
-  int64_t i = r0;
-  if (full_cols) {
-    for (; i + U <= r1; i += U) {
-      Vec<VW> a[U];
-      float xv[U];
+  for (int64_t i = r0; i < r1;) {
+    const int64_t ge = i + kGroupRows < r1 ? i + kGroupRows : r1;
+    float gs[VW];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        ld_stream(A + (i + u) * lda + c0, a[u]);
-        xv[u] = __ldg(x + i + u);
+    for (int l = 0; l < VW; ++l) gs[l] = 0.f;
+    if (full_cols) {
+      for (; i + U <= ge; i += U) {
+        Vec<VW> a[U];
+        float xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          ld_stream(A + (i + u) * lda + c0, a[u]);
+          xv[u] = __ldg(x + i + u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int l = 0; l < VW; ++l) gs[l] = __fadd_rn(gs[l], __fmul_rn(a[u].v[l], xv[u]));
       }
+      for (; i < ge; ++i) {
+        Vec<VW> a;
+        ld_stream(A + i * lda + c0, a);
+        const float xv = __ldg(x + i);
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+        for (int l = 0; l < VW; ++l) gs[l] = __fadd_rn(gs[l], __fmul_rn(a.v[l], xv));
+      }
+    } else {
+      for (; i < ge; ++i) {
+        const float xv = __ldg(x + i);
 #pragma unroll
-        for (int l = 0; l < VW; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a[u].v[l], xv[u]));
+        for (int l = 0; l < VW; ++l)
+          if (c0 + l < N) gs[l] = __fadd_rn(gs[l], __fmul_rn(__ldg(A + i * lda + c0 + l), xv));
+      }
     }
-    for (; i < r1; ++i) {
-      Vec<VW> a;
-      ld_stream(A + i * lda + c0, a);
-      const float xv = __ldg(x + i);
 #pragma unroll
-      for (int l = 0; l < VW; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a.v[l], xv));
-    }
-  } else {
-    for (; i < r1; ++i) {
-      const float xv = __ldg(x + i);
-#pragma unroll
-      for (int l = 0; l < VW; ++l)
-        if (c0 + l < N) acc[l] = __fadd_rn(acc[l], __fmul_rn(__ldg(A + i * lda + c0 + l), xv));
-    }
+    for (int l = 0; l < VW; ++l) neumaier_add(acc[l], cmp[l], gs[l]);
   }
+#pragma unroll
+  for (int l = 0; l < VW; ++l) acc[l] = neumaier_value(acc[l], cmp[l]);
 }
 
 template <int THREADS, int VW, int U, int PASSES>
@@ -123,17 +145,17 @@ __global__ void __launch_bounds__(THREADS)
     for (int l = 0; l < VW; ++l) {
       const int64_t j = c0 + l;
       if (j >= N) continue;
-      float s = 0.f;
+      float s = 0.f, c = 0.f;              // block partials added in order, compensated
       int64_t q = 0;
-      for (; q + 8 <= RB; q += 8) {        // eight loads in flight, added in order
+      for (; q + 8 <= RB; q += 8) {        // eight loads in flight
         float v[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = __ldcg(partials + (q + k) * N + j);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s = __fadd_rn(s, v[k]);
+        for (int k = 0; k < 8; ++k) neumaier_add(s, c, v[k]);
       }
-      for (; q < RB; ++q) s = __fadd_rn(s, __ldcg(partials + q * N + j));
-      const float z = __fmul_rn(alpha, s);
+      for (; q < RB; ++q) neumaier_add(s, c, __ldcg(partials + q * N + j));
+      const float z = __fmul_rn(alpha, neumaier_value(s, c));
       y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
     }
     if (threadIdx.x == 0) tickets[cb] = 0u;   // ready for the next call
@@ -142,8 +164,8 @@ __global__ void __launch_bounds__(THREADS)
 
 // Second pass: column j's RB partials P[j][0..RB) -> y_j.  Warp w of the
 // grid takes columns w, w + W, ...; lane l folds partials l, l+32, ...
-// (eight loads in flight, added in order), then a halving tree over the
-// lanes (shuffle-down 16, 8, 4, 2, 1).
+// (eight loads in flight, added in order with Neumaier's compensated step),
+// then a halving tree over the lanes (shuffle-down 16, 8, 4, 2, 1).
 __global__ void __launch_bounds__(256)
     gemv_t_combine(int64_t N, int64_t RB, float alpha, float beta,
                    const float* __restrict__ partials, float* __restrict__ y) {
@@ -152,16 +174,17 @@ __global__ void __launch_bounds__(256)
   const int64_t W = (int64_t)gridDim.x * (blockDim.x / kWarp);
   for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp; j < N; j += W) {
     const float* p = partials + j * RB;
-    float s = 0.f;
+    float s = 0.f, c = 0.f;              // the lane's partials in order, compensated
     int64_t q = lane;
     for (; q + 7 * kWarp < RB; q += 8 * kWarp) {
       float v[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + q + k * kWarp);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) s = __fadd_rn(s, v[k]);
+      for (int k = 0; k < 8; ++k) neumaier_add(s, c, v[k]);
     }
-    for (; q < RB; q += kWarp) s = __fadd_rn(s, __ldcg(p + q));
+    for (; q < RB; q += kWarp) neumaier_add(s, c, __ldcg(p + q));
+    s = neumaier_value(s, c);
 #pragma unroll
     for (int o = kWarp / 2; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
     if (lane == 0) {
@@ -178,9 +201,10 @@ __global__ void __launch_bounds__(256)
 // cluster in rank (= block) order through distributed shared memory, and
 // writes one partial per column and cluster, P[c][j] (c = rb / CL).  The
 // CTA that arrives last at the ticket of (column block, slice) adds the
-// RB / CL cluster partials of the slice's columns in cluster order (all its
-// loads in flight) and writes y.  Per column:
-//   s = reduce-seq(add, 0) over clusters of reduce-seq(add, 0) over the CL
+// RB / CL cluster partials of the slice's columns in cluster order with
+// Neumaier's compensated step (sixteen loads in flight) and writes y.  Per
+// column:
+//   s = reduce-seq-comp over clusters of reduce-seq(add, 0) over the CL
 //       block partials of the cluster;   y_j = fl(alpha*s) (+ fl(beta*y_j)).
 template <int THREADS, int VW, int U, int CL>
 __global__ void __launch_bounds__(THREADS)
@@ -223,17 +247,17 @@ __global__ void __launch_bounds__(THREADS)
   for (int k = threadIdx.x; k < SL; k += THREADS) {
     const int64_t j = cb * CB + q * SL + k;
     if (j >= N) continue;
-    float s = 0.f;
+    float s = 0.f, c = 0.f;                     // cluster partials in order, compensated
     int64_t e = 0;
-    for (; e + 16 <= RBC; e += 16) {            // sixteen loads in flight, added in order
+    for (; e + 16 <= RBC; e += 16) {            // sixteen loads in flight
       float v[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) v[u] = __ldcg(partials + (e + u) * N + j);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) s = __fadd_rn(s, v[u]);
+      for (int u = 0; u < 16; ++u) neumaier_add(s, c, v[u]);
     }
-    for (; e < RBC; ++e) s = __fadd_rn(s, __ldcg(partials + e * N + j));
-    const float z = __fmul_rn(alpha, s);
+    for (; e < RBC; ++e) neumaier_add(s, c, __ldcg(partials + e * N + j));
+    const float z = __fmul_rn(alpha, neumaier_value(s, c));
     y[j] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[j]));
   }
   if (threadIdx.x == 0) *ticket = 0u;           // ready for the next call

@@ -100,8 +100,11 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
     return;
   }
 
-  // consumer warps: warp w folds row (block start + w)
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  // consumer warps: warp w folds row (block start + w); lane l's vectors of
+  // a row are l, l+32, ... (J per chunk), grouped kGemvGroup at a time
+  static_assert(J % kGemvGroup == 0 || kGemvGroup % J == 0, "groups align with chunks");
+  GroupedDot<4> acc;
+  acc.init();
   for (int64_t k = 0; k < total; ++k) {
     const int s = static_cast<int>(k % S);
     if (!mbar_wait(&full_bar[s], static_cast<uint32_t>((k / S) & 1))) {
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
     const int64_t blk = k / nchunks, ch = k % nchunks;
     const int64_t row = r_begin + blk * WARPS + warp;
     const int64_t cw = N - ch * C < C ? N - ch * C : C;
-    if (ch == 0) acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+    if (ch == 0) acc.init();
     if (row < r_end) {
       const float* st = buf + (size_t)s * kStageFloats;
 #pragma unroll
@@ -125,8 +128,13 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
           a.v[0] = a.v[1] = a.v[2] = a.v[3] = 0.f;
           v = a;
         }
-#pragma unroll
-        for (int l = 0; l < 4; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a.v[l], v.v[l]));
+        acc.add(a, v);
+        if constexpr (J % kGemvGroup == 0) {
+          if ((j + 1) % kGemvGroup == 0) acc.flush();
+        }
+      }
+      if constexpr (J % kGemvGroup != 0) {   // a group spans several chunks
+        if ((ch + 1) % (kGemvGroup / J) == 0) acc.flush();
       }
     }
     __syncwarp();
@@ -134,8 +142,7 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty_bar[s]))
                    : "memory");
     if (ch == nchunks - 1 && row < r_end) {
-      float r = __fadd_rn(__fadd_rn(__fadd_rn(acc[0], acc[1]), acc[2]), acc[3]);
-      r = warp_tree(r);
+      float r = warp_tree(acc.value());
       if (lane == 0) {
         const float z = __fmul_rn(alpha, r);
         y[row] = beta == 0.f ? z : __fadd_rn(z, __fmul_rn(beta, y[row]));

@@ -174,6 +174,61 @@ __device__ __forceinline__ void st_smem(float* p, const Vec<VW>& o) {
   }
 }
 
+// Neumaier's compensated step (Neumaier 1974): s + t rounded, and the
+// rounding error of that add (exact: Fast2Sum with the larger operand
+// first) added to the running compensation c.  A lane that adds its tile
+// sums this way carries an error of about 2u|sum| however many tiles it
+// folds, instead of one rounding per tile.
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float t) {
+  const float u = __fadd_rn(s, t);
+  const float d = fabsf(s) >= fabsf(t) ? __fadd_rn(__fsub_rn(s, u), t)
+                                       : __fadd_rn(__fsub_rn(t, u), s);
+  s = u;
+  c = __fadd_rn(c, d);
+}
+// The compensated value s + c; a non-finite s (Inf or NaN among the terms)
+// is returned as it is, so that Inf does not turn into NaN.
+__device__ __forceinline__ float neumaier_value(float s, float c) {
+  return isfinite(s) ? __fadd_rn(s, c) : s;
+}
+
+// Vectors a gemv lane (or thread) folds plainly before it adds their value
+// to its compensated sum: its vectors k = 0, 1, ... of a row (or segment)
+// form groups gG .. gG+G-1; a group's products are folded from zero over
+// the VW lanes, the lanes added in order, and the group values added with
+// neumaier_add, so a row's error does not grow with its length.
+constexpr int kGemvGroup = 8;
+
+template <int VW>
+struct GroupedDot {
+  float gs[VW];        // the current group's lane sums
+  float s, c;          // compensated sum of the finished groups
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int l = 0; l < VW; ++l) gs[l] = 0.f;
+    s = c = 0.f;
+  }
+  __device__ __forceinline__ void add(const Vec<VW>& a, const Vec<VW>& b) {
+#pragma unroll
+    for (int l = 0; l < VW; ++l) gs[l] = __fadd_rn(gs[l], __fmul_rn(a.v[l], b.v[l]));
+  }
+  // close the current group (a partial group is closed the same way: the
+  // zeros that would pad it change nothing)
+  __device__ __forceinline__ void flush() {
+    float v = gs[0];
+#pragma unroll
+    for (int l = 1; l < VW; ++l) v = __fadd_rn(v, gs[l]);
+    neumaier_add(s, c, v);
+#pragma unroll
+    for (int l = 0; l < VW; ++l) gs[l] = 0.f;
+  }
+  // the value after the last vector (closes the last group)
+  __device__ __forceinline__ float value() {
+    flush();
+    return neumaier_value(s, c);
+  }
+};
+
 // Halving tree over the 32 lanes of a warp: at offset o lane j adds lane
 // j + o (iterate-5 of split-2 after reorder-stride with n = 2).  Lane 0 ends
 // with the warp's value.

@@ -21,6 +21,12 @@
 //    read through distributed shared memory;
 //  * the outer reduce: per-CTA fp32 partials summed in FP64 either by the
 //    last CTA to finish (one pass, atomic ticket) or by a second kernel.
+// Within a thread the fold is split at the tile (the partial reduction of
+// Fig. 3d applied to the thread's reduce-seq): each tile's J vectors are
+// folded from zero into VW lane sums, the lanes are added in order, and the
+// thread adds its tile values with Neumaier's compensated step, so its error
+// does not grow with the number of tiles it folds (the thread's value is
+// sum + compensation).
 // Every add and multiply is an explicit round-to-nearest fp32 operation
 // (__fadd_rn / __fmul_rn), so the result is the expression's value bit for
 // bit.  STAGES >= 2 stages full tiles through a ring of TMA bulk copies
@@ -64,6 +70,15 @@ template <int OP, int VW>
 __device__ __forceinline__ void fold_vec(float* acc, const Vec<VW>& a, const Vec<VW>& b) {
 #pragma unroll
   for (int l = 0; l < VW; ++l) acc[l] = fold_term<OP>(acc[l], a.v[l], b.v[l]);
+}
+
+// lane sum of a tile: ((l0 + l1) + l2) + ...
+template <int VW>
+__device__ __forceinline__ float lane_sum(const float* ts) {
+  float r = ts[0];
+#pragma unroll
+  for (int l = 1; l < VW; ++l) r = __fadd_rn(r, ts[l]);
+  return r;
 }
 
 // index (in vectors) of thread t's j-th vector inside a tile
@@ -145,9 +160,7 @@ __global__ void __launch_bounds__(THREADS)
   __shared__ double red64[kWarp];
   const int t = threadIdx.x;
   const int64_t full = n / TILE;
-  float acc[VW];
-#pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = 0.0f;
+  float acc = 0.0f, cmp = 0.0f;
 
   Vec<VW> cx[J], cy[J];
   int64_t tile = blockIdx.x;
@@ -170,8 +183,12 @@ __global__ void __launch_bounds__(THREADS)
         if constexpr (OP == LIFT_OP_DOT) ld_stream(y + e, ny[j]);
       }
     }
+    float ts[VW];
 #pragma unroll
-    for (int j = 0; j < J; ++j) fold_vec<OP, VW>(acc, cx[j], cy[j]);
+    for (int l = 0; l < VW; ++l) ts[l] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < J; ++j) fold_vec<OP, VW>(ts, cx[j], cy[j]);
+    neumaier_add(acc, cmp, lane_sum<VW>(ts));
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       cx[j] = nx[j];
@@ -179,11 +196,15 @@ __global__ void __launch_bounds__(THREADS)
     }
     tile = nxt;
   }
-  if (tile == full && full * TILE < n) fold_tail<OP, THREADS, TILE, VW, STRIDE>(acc, x, y, n, tile);
-
-  float r = acc[0];
+  if (tile == full && full * TILE < n) {
+    float ts[VW];
 #pragma unroll
-  for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
+    for (int l = 0; l < VW; ++l) ts[l] = 0.0f;
+    fold_tail<OP, THREADS, TILE, VW, STRIDE>(ts, x, y, n, tile);
+    neumaier_add(acc, cmp, lane_sum<VW>(ts));
+  }
+
+  const float r = neumaier_value(acc, cmp);
   finish<OP, THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
   (void)status;
   (void)polls;
@@ -225,9 +246,7 @@ __global__ void __launch_bounds__(THREADS)
   if (t == 0)
     for (int64_t k = 0; k < STAGES && k < myK; ++k) issue(k);
 
-  float acc[VW];
-#pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = 0.0f;
+  float acc = 0.0f, cmp = 0.0f;
   bool timed_out = false;
   int64_t k = 0;
   for (; k < myK; ++k) {
@@ -235,14 +254,18 @@ __global__ void __launch_bounds__(THREADS)
     const bool ok = mbar_wait(&full_bar[s], static_cast<uint32_t>((k / STAGES) & 1), polls);
     if (ok) {
       const float* bx = buf + (size_t)s * NIN * TILE;
+      float ts[VW];
+#pragma unroll
+      for (int l = 0; l < VW; ++l) ts[l] = 0.0f;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int idx = vec_index<THREADS, J, STRIDE>(t, j) * VW;
         Vec<VW> a, b;
         ld_smem<VW>(bx + idx, a);
         if constexpr (OP == LIFT_OP_DOT) ld_smem<VW>(bx + TILE + idx, b);
-        fold_vec<OP, VW>(acc, a, b);
+        fold_vec<OP, VW>(ts, a, b);
       }
+      neumaier_add(acc, cmp, lane_sum<VW>(ts));
     }
     if (!__syncthreads_and(ok)) {
       // a copy did not complete in time: record it, wait (with the full
@@ -261,12 +284,15 @@ __global__ void __launch_bounds__(THREADS)
     if (t == 0 && k + STAGES < myK) issue(k + STAGES);
   }
   const int64_t tail_owner = full % G;
-  if (!timed_out && full * TILE < n && (int64_t)blockIdx.x == tail_owner)
-    fold_tail<OP, THREADS, TILE, VW, STRIDE>(acc, x, y, n, full);
-
-  float r = acc[0];
+  if (!timed_out && full * TILE < n && (int64_t)blockIdx.x == tail_owner) {
+    float ts[VW];
 #pragma unroll
-  for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
+    for (int l = 0; l < VW; ++l) ts[l] = 0.0f;
+    fold_tail<OP, THREADS, TILE, VW, STRIDE>(ts, x, y, n, full);
+    neumaier_add(acc, cmp, lane_sum<VW>(ts));
+  }
+
+  float r = neumaier_value(acc, cmp);
   if (timed_out) r = __int_as_float(0x7fc00000);
   finish<OP, THREADS, CLUSTER, ONEPASS>(r, red, red64, partials, ticket, result, result64);
 }

@@ -288,12 +288,6 @@ __device__ __forceinline__ void ld_x(const float* p, Vec<VW>& o) {
   }
 }
 
-template <int VW>
-__device__ __forceinline__ void fold_dot(float* acc, const Vec<VW>& a, const Vec<VW>& b) {
-#pragma unroll
-  for (int l = 0; l < VW; ++l) acc[l] = __fadd_rn(acc[l], __fmul_rn(a.v[l], b.v[l]));
-}
-
 template <int WARPS, int VW, int UNROLL>
 __global__ void __launch_bounds__(WARPS * kWarp)
     gemv_warp(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
@@ -303,12 +297,12 @@ __global__ void __launch_bounds__(WARPS * kWarp)
   const int64_t gw = (int64_t)blockIdx.x * WARPS + threadIdx.x / kWarp;
   const int64_t total = (int64_t)gridDim.x * WARPS;
   const int64_t chunks = N / kChunk;
+  static_assert(kGemvGroup % UNROLL == 0, "an unrolled step stays inside one group");
   for (int64_t row = gw; row < M; row += total) {
     const float* a = A + row * lda;
-    float acc[VW];
-#pragma unroll
-    for (int l = 0; l < VW; ++l) acc[l] = 0.0f;
-    int64_t c = 0;
+    GroupedDot<VW> acc;
+    acc.init();
+    int64_t c = 0;                     // the lane's vector index along the row
     for (; c + UNROLL <= chunks; c += UNROLL) {
       Vec<VW> va[UNROLL], vx[UNROLL];
 #pragma unroll
@@ -318,26 +312,25 @@ __global__ void __launch_bounds__(WARPS * kWarp)
         ld_x<VW>(x + e, vx[u]);
       }
 #pragma unroll
-      for (int u = 0; u < UNROLL; ++u) fold_dot<VW>(acc, va[u], vx[u]);
+      for (int u = 0; u < UNROLL; ++u) acc.add(va[u], vx[u]);
+      if ((c + UNROLL) % kGemvGroup == 0) acc.flush();
     }
     for (; c < chunks; ++c) {
       Vec<VW> va, vx;
       const int64_t e = c * kChunk + lane * VW;
       ld_stream(a + e, va);
       ld_x<VW>(x + e, vx);
-      fold_dot<VW>(acc, va, vx);
+      acc.add(va, vx);
+      if ((c + 1) % kGemvGroup == 0) acc.flush();
     }
     if (chunks * kChunk < N) {
       Vec<VW> va, vx;
       const int64_t e = chunks * kChunk + lane * VW;
       ld_guarded<VW>(a, e, N, va);
       ld_guarded<VW>(x, e, N, vx);
-      fold_dot<VW>(acc, va, vx);
+      acc.add(va, vx);
     }
-    float r = acc[0];
-#pragma unroll
-    for (int l = 1; l < VW; ++l) r = __fadd_rn(r, acc[l]);
-    r = warp_tree(r);
+    float r = warp_tree(acc.value());
     if (lane == 0) {
       const float z = __fmul_rn(alpha, r);
       y[row] = (beta == 0.0f) ? z : __fadd_rn(z, __fmul_rn(beta, y[row]));

@@ -172,3 +172,65 @@ def test_fp32_mode_rounds_each_operation():
     assert got == np.float32(exact) and got.dtype == np.float32
     with pytest.raises(ValueError):
         evaluate(Map(abs_), np.array([0.1]), mode="f32")   # 0.1 is not an fp32 value
+
+
+# ---------------------------------------------------------------------------
+# the compensated reduce-seq (Neumaier's summation) used for the lane folds
+# ---------------------------------------------------------------------------
+def test_reduce_seq_comp_exact_on_integers():
+    from oracle.patterns import ReduceSeqComp
+    rng = np.random.default_rng(3)
+    x = rng.integers(-1000, 1000, 777)
+    assert evaluate(ReduceSeqComp(), x, mode="int")[0] == int(x.sum())
+    assert evaluate(ReduceSeqComp(), x.astype(float))[0] == float(x.sum())
+
+
+def test_reduce_seq_comp_recovers_what_a_plain_fold_loses():
+    # 1 followed by 100 terms of 2^-24: each plain fp32 add is a tie that
+    # rounds back to 1 (round to even), so the plain left fold returns 1;
+    # the exact sum 1 + 100 * 2^-24 = 1 + 50 * 2^-23 is an fp32 number, and
+    # the compensated fold returns it exactly
+    from oracle.patterns import ReduceSeqComp
+    x = np.concatenate([[1.0], np.full(100, 2.0 ** -24)])
+    assert evaluate(ReduceSeq(add, 0), x, mode="f32")[0] == np.float32(1.0)
+    assert evaluate(ReduceSeqComp(), x, mode="f32")[0] == np.float32(1.0 + 100 * 2.0 ** -24)
+    # the smaller operand first (the other branch of the correction)
+    y = np.concatenate([np.full(100, 2.0 ** -24), [1.0], np.full(100, -(2.0 ** -24))])
+    assert evaluate(ReduceSeqComp(), y, mode="f32")[0] == np.float32(1.0)
+
+
+def test_reduce_seq_comp_keeps_inf_and_nan():
+    from oracle.patterns import ReduceSeqComp
+    assert evaluate(ReduceSeqComp(), np.array([1.0, np.inf, 2.0]), mode="f32")[0] == np.inf
+    assert evaluate(ReduceSeqComp(), np.array([1.0, -np.inf, 2.0]), mode="f32")[0] == -np.inf
+    assert np.isnan(evaluate(ReduceSeqComp(), np.array([1.0, np.nan, 2.0]), mode="f32")[0])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_reduce_seq_comp_within_two_units_of_the_exact_sum(seed):
+    # Neumaier's bound: |s_comp - S| <= 2u|S| + 2 m^2 u^2 sum|x_i| (u = 2^-24)
+    import math
+    from oracle.patterns import ReduceSeqComp
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(3000) * np.exp(rng.uniform(-8, 8, 3000))).astype(np.float32)
+    exact = math.fsum(float(v) for v in x)
+    got = float(evaluate(ReduceSeqComp(), x.astype(np.float64), mode="f32")[0])
+    u = 2.0 ** -24
+    bound = 2 * u * abs(exact) + 2 * (3000 * u) ** 2 * float(np.abs(x.astype(np.float64)).sum())
+    assert abs(got - exact) <= bound
+    # a plain fp32 left fold of the same terms is typically far worse
+    plain = float(evaluate(ReduceSeq(add, 0), x.astype(np.float64), mode="f32")[0])
+    assert abs(got - exact) <= abs(plain - exact)
+
+
+def test_reduce_seq_comp_lanes():
+    # vect^4(add): four independent compensated folds, lane by lane
+    from oracle.patterns import ReduceSeqComp, Vect
+    x = np.zeros((101, 4))
+    x[0] = [1.0, 2.0, 4.0, 8.0]
+    x[1:] = 2.0 ** -24
+    got = evaluate(C(ReduceSeqComp(Vect(4, add)), AsVector(4)), x.reshape(-1), mode="f32")
+    assert got.shape[-1] == 4
+    # each lane returns the fp32 rounding of its exact sum
+    for k, base in enumerate([1.0, 2.0, 4.0, 8.0]):
+        assert got[0, k] == np.float32(base + 100 * 2.0 ** -24)
