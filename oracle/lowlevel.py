@@ -277,7 +277,7 @@ def gemv_split_z_variant(M: int, N: int, alpha, vw: int, threads: int, L: int, S
 
 
 def gemv_t_z_variant(M: int, N: int, alpha, B: int, RB: int, passes: int = 1,
-                     cluster: int = 1, group: int = 16):
+                     cluster: int = 1, group: int = 32):
     """z of the gemv-T kernel: every column of A (the rows of the
     reorder-stride view) zipped with x, padded to RB*B, folded in RB blocks
     of B rows (fp32; a block's rows in groups of ``group``, each group

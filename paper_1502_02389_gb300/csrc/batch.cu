@@ -182,7 +182,7 @@ __device__ void gemv_item(const OpDev& o, int64_t r0, int64_t r1) {
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) acc.add(va[u], vx[u]);
-      if ((c + U) % kGemvGroup == 0) acc.flush();
+      if (((c + U) & (kGemvGroup - 1)) == 0) acc.flush();
     }
     for (; c < chunks; ++c) {
       Vec<VW> va, vx;
@@ -190,7 +190,7 @@ __device__ void gemv_item(const OpDev& o, int64_t r0, int64_t r1) {
       ld_stream(a + e, va);
       ld_x<VW>(o.x + e, vx);
       acc.add(va, vx);
-      if ((c + 1) % kGemvGroup == 0) acc.flush();
+      if (((c + 1) & (kGemvGroup - 1)) == 0) acc.flush();
     }
     if (chunks * kChunk < o.N) {
       Vec<VW> va, vx;

@@ -71,14 +71,14 @@ __global__ void __launch_bounds__(THREADS)
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) acc.add(a[u], b[u]);
-    if ((k + U) % kGemvGroup == 0) acc.flush();
+    if (((k + U) & (kGemvGroup - 1)) == 0) acc.flush();
   }
   for (; c + VW <= c_end; c += kStep, ++k) {
     Vec<VW> a, b;
     ld_stream(row + c, a);
     ld_x_vec<VW>(x + c, b);
     acc.add(a, b);
-    if ((k + 1) % kGemvGroup == 0) acc.flush();
+    if (((k + 1) & (kGemvGroup - 1)) == 0) acc.flush();
   }
   if (c < c_end) {           // the ragged last vector of the row
     Vec<VW> a, b;

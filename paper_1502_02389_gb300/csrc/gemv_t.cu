@@ -10,12 +10,12 @@
 //   map(mult(alpha)) . COMBINE . join . map(BLOCK) . split^B . pad-(RB*B)
 //     . zip(col_j, x)
 //   BLOCK = reduce-seq-comp . join . map(reduce-seq(lambda acc,(a,b):
-//             acc + a*b, 0)) . split^16 . pad
+//             acc + a*b, 0)) . split^32 . pad
 // (reduce-seq-comp: Neumaier's compensated reduce-seq)
 //
 // i.e. the column is split into RB uniform blocks of B rows (the last one
 // padded with zeros); CTA (cb, rb) folds the rows of block rb -- in groups
-// of 16 rows folded in order, the group sums added with Neumaier's
+// of 32 rows folded in order, the group sums added with Neumaier's
 // compensated step -- for
 // its THREADS*VW consecutive columns (thread t owns VW adjacent columns, so
 // a warp reads 32*VW*4 contiguous bytes of every row) and writes one fp32
@@ -51,7 +51,7 @@ lift_status launch_rows_combine(int64_t n, int64_t per, float alpha, float beta,
 namespace {
 
 // Rows folded plainly before a compensated add (see fold_rows).
-constexpr int kGroupRows = 16;
+constexpr int kGroupRows = 32;
 
 // Row block [r0, r1) of this thread's VW columns c0 .. c0+VW-1 (zero for an
 // empty block): the rows in groups of kGroupRows, each group's products
@@ -78,9 +78,21 @@ __device__ __forceinline__ void fold_rows(int64_t N, const float* __restrict__ A
         Vec<VW> a[U];
         float xv[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          ld_stream(A + (i + u) * lda + c0, a[u]);
-          xv[u] = __ldg(x + i + u);
+        for (int u = 0; u < U; ++u) ld_stream(A + (i + u) * lda + c0, a[u]);
+        if constexpr (VW >= 4 && U % 4 == 0) {
+          // row blocks start at multiples of 4 rows and x is 16-byte aligned
+          // for these variants: x[i .. i+U) in 16-byte loads
+#pragma unroll
+          for (int u = 0; u < U; u += 4) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(x + i + u));
+            xv[u] = q.x;
+            xv[u + 1] = q.y;
+            xv[u + 2] = q.z;
+            xv[u + 3] = q.w;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u) xv[u] = __ldg(x + i + u);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -267,6 +279,7 @@ constexpr int kCombineThreads = 256;
 constexpr int64_t kMaxRowBlocks2 = 512;   // two pass: at most 16 partials per lane
 
 constexpr int kTicketBase = 64;    // gemv-T tickets follow the reductions' counters
+constexpr int64_t kBlockAlign = 4; // rows per block: a multiple of 4 (16-byte x loads)
 
 template <int THREADS, int VW, int U, int PASSES>
 struct GemvT {
@@ -288,6 +301,7 @@ struct GemvT {
     if (want > a.M) want = a.M;
     if (want < 1) want = 1;
     B = (a.M + want - 1) / want;
+    B = (B + kBlockAlign - 1) / kBlockAlign * kBlockAlign;
     RB = (a.M + B - 1) / B;
   }
   static int64_t grid(const Variant&, const Args& a) {
@@ -338,6 +352,7 @@ struct GemvTCluster {
     if (want > a.M) want = a.M;
     if (want < 1) want = 1;
     B = (a.M + want - 1) / want;
+    B = (B + kBlockAlign - 1) / kBlockAlign * kBlockAlign;
     RB = (a.M + B - 1) / B;
     RB = (RB + CL - 1) / CL * CL;
   }

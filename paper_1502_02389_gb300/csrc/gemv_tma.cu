@@ -130,7 +130,7 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
         }
         acc.add(a, v);
         if constexpr (J % kGemvGroup == 0) {
-          if ((j + 1) % kGemvGroup == 0) acc.flush();
+          if (((j + 1) & (kGemvGroup - 1)) == 0) acc.flush();
         }
       }
       if constexpr (J % kGemvGroup != 0) {   // a group spans several chunks

@@ -197,16 +197,19 @@ __device__ __forceinline__ float neumaier_value(float s, float c) {
 // form groups gG .. gG+G-1; a group's products are folded from zero over
 // the VW lanes, the lanes added in order, and the group values added with
 // neumaier_add, so a row's error does not grow with its length.
-constexpr int kGemvGroup = 8;
+constexpr int kGemvGroup = 8;   // a power of two
+static_assert((kGemvGroup & (kGemvGroup - 1)) == 0, "group masks need a power of two");
 
 template <int VW>
 struct GroupedDot {
   float gs[VW];        // the current group's lane sums
   float s, c;          // compensated sum of the finished groups
+  bool closed;         // some group was closed before the last one
   __device__ __forceinline__ void init() {
 #pragma unroll
     for (int l = 0; l < VW; ++l) gs[l] = 0.f;
     s = c = 0.f;
+    closed = false;
   }
   __device__ __forceinline__ void add(const Vec<VW>& a, const Vec<VW>& b) {
 #pragma unroll
@@ -214,16 +217,23 @@ struct GroupedDot {
   }
   // close the current group (a partial group is closed the same way: the
   // zeros that would pad it change nothing)
-  __device__ __forceinline__ void flush() {
+  __device__ __forceinline__ float lanes() const {
     float v = gs[0];
 #pragma unroll
     for (int l = 1; l < VW; ++l) v = __fadd_rn(v, gs[l]);
-    neumaier_add(s, c, v);
+    return v;
+  }
+  __device__ __forceinline__ void flush() {
+    neumaier_add(s, c, lanes());
 #pragma unroll
     for (int l = 0; l < VW; ++l) gs[l] = 0.f;
+    closed = true;
   }
-  // the value after the last vector (closes the last group)
+  // the value after the last vector (closes the last group); with a single
+  // group the compensated sum is that group's value itself (0 + v is exact
+  // and its correction is 0), so it is returned directly
   __device__ __forceinline__ float value() {
+    if (!closed) return lanes();
     flush();
     return neumaier_value(s, c);
   }

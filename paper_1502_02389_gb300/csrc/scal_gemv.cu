@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(WARPS * kWarp)
       }
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) acc.add(va[u], vx[u]);
-      if ((c + UNROLL) % kGemvGroup == 0) acc.flush();
+      if (((c + UNROLL) & (kGemvGroup - 1)) == 0) acc.flush();
     }
     for (; c < chunks; ++c) {
       Vec<VW> va, vx;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(WARPS * kWarp)
       ld_stream(a + e, va);
       ld_x<VW>(x + e, vx);
       acc.add(va, vx);
-      if ((c + 1) % kGemvGroup == 0) acc.flush();
+      if (((c + 1) & (kGemvGroup - 1)) == 0) acc.flush();
     }
     if (chunks * kChunk < N) {
       Vec<VW> va, vx;
