@@ -3,10 +3,10 @@
 Default workload (the dot/scal configuration): fp32 vectors x, y of
 n = 2^26 elements ~ N(0,1) (seed 1), alpha = 1.5.  One step is
 dot(x, y) and scal(alpha, x) -> z with the variants the cost model picks,
-submitted through the C-ABI as one batched persistent launch
-(``--mode batched``, the default) or as two calls (``--mode calls``); the
-other submission is measured too and reported in ``config``, with the
-learned pick's slowdown against an on-the-spot exhaustive sweep of each op.  The metric is HBM GB/s of algorithmic traffic
+submitted through the C-ABI as two calls (``--mode calls``, the default)
+or as one batched persistent launch (``--mode batched``); the other
+submission is measured too and reported in ``config``, with the learned
+pick's slowdown against an on-the-spot exhaustive sweep of each op.  The metric is HBM GB/s of algorithmic traffic
 (dot reads 8n bytes, scal reads 4n and writes 4n bytes; 16n per step) and
 its fraction of the measured HBM peak.  Inputs (3 x 256 MiB) exceed the
 129 MB L2, so no flush is needed between steps.
@@ -18,14 +18,15 @@ dot/scal workload on one GPU) also measures asum, both gemv shapes, mixed
 and batch after the headline step, each with its own roofline, oracle check
 and CPU baseline, under ``config.sub`` (``--no-sub`` skips them).
 
-Single-call workloads (asum_large, gemv, gemv-T, mixed, BlackScholes) submit
-their K timed steps as one CUDA graph replay (``--submit graph``, the
-default: the calls run back to back with no host launch between them, as a
-captured loop of calls runs); each kernel's duration comes from a graph of K
-launches of that call alone, timed with events on the replaying stream.  The
-same steps submitted one host call at a time (events around each call) are
-reported in ``config.eager``.  The dot/scal step is one launch of the
-library's own captured batch graph per step.
+Workloads whose step is a few plain calls (dot/scal, asum_large, gemv,
+gemv-T, mixed, BlackScholes) submit their K timed steps as one CUDA graph
+replay (``--submit graph``, the default: the calls run back to back with no
+host launch between them, as a captured loop of calls runs); each call's
+duration comes from a graph of K launches of that call alone, timed with
+events on the replaying stream.  The same steps submitted one host call at a
+time (events around each call) are reported in ``config.eager``.  The
+batched dot/scal step (``--mode batched``) is one launch of the library's
+own captured batch graph per step.
 
 Under torchrun each rank runs its own replica on its own GPU (the ops of
 one step do not exchange data); value is the bytes of all ranks divided by
@@ -334,6 +335,8 @@ def run_ours(args, rank, world, dist):
             kdot = ["dot:" + pd["name"], 8 * n, [], []]
             kscal = ["scal:" + ps["name"], 8 * n, [], []]
             kernels = [kdot, kscal]
+            graph_calls = [(kdot, lambda: lift.lift_dot_v(vd, x, y, n, r)),
+                           (kscal, lambda: lift.lift_scal_v(vs, n, float(alpha), x, z))]
 
             def step(timed):
                 if timed:
@@ -1235,8 +1238,9 @@ def main():
                     help="dot_scal: skip the records of the other configurations")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the on-the-spot variant sweep and the other submission mode")
-    ap.add_argument("--mode", default="batched", choices=["batched", "calls"],
-                    help="dot_scal: submit the step as one batched launch or as two calls")
+    ap.add_argument("--mode", default="calls", choices=["batched", "calls"],
+                    help="dot_scal: submit the step as two calls (default; with --submit graph "
+                         "the timed steps run as one CUDA graph) or as one batched launch")
     ap.add_argument("--fixed-policy", action="store_true",
                     help="use the FIXED variant policy instead of the trained cost model")
     ap.add_argument("--batch-ops", type=int, default=20000,
