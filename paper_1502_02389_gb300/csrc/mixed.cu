@@ -202,7 +202,11 @@ __device__ __forceinline__ void fold_block_guarded(Comp& acc, const void* x, con
   two_sum_add(acc, bs);
 }
 
-template <int OP, int DT, int THREADS, int U, bool GUARDED>
+// CONTIG: a CTA step takes U consecutive blocks (super-block sb covers
+// blocks sb*U .. sb*U+U-1, CTAs take super-blocks round robin), so each step
+// reads one contiguous U*4096-element run; otherwise the U blocks of a step
+// are b, b+G, ..., b+(U-1)G.
+template <int OP, int DT, int THREADS, int U, bool GUARDED, bool CONTIG = false>
 __global__ void __launch_bounds__(THREADS)
     mixed_reduce(const void* __restrict__ x, const float* __restrict__ xs, const void* __restrict__ y,
                  const float* __restrict__ ys, int64_t n, double* __restrict__ partials,
@@ -213,7 +217,29 @@ __global__ void __launch_bounds__(THREADS)
   const int64_t full = n / kBlock;
   Comp acc{0.f, 0.f};
   int64_t b = blockIdx.x;
-  if constexpr (!GUARDED) {
+  if constexpr (CONTIG && !GUARDED) {
+    const int64_t nsb = full / U;
+    for (int64_t sb = blockIdx.x; sb < nsb; sb += G) {
+      Raw<DT, E> rx[U], ry[U];
+      float sc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t blk = sb * U + u;
+        load_raw<DT, E>(x, blk * kBlock + (int64_t)t * E, rx[u]);
+        if constexpr (OP == LIFT_OP_DOT) load_raw<DT, E>(y, blk * kBlock + (int64_t)t * E, ry[u]);
+        sc[u] = block_scale<OP, DT>(xs, ys, blk);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) fold_block<OP, DT, E>(acc, rx[u], ry[u], sc[u]);
+    }
+    for (int64_t bb = nsb * U + blockIdx.x; bb < full; bb += G) {   // full blocks left over
+      Raw<DT, E> rx, ry;
+      load_raw<DT, E>(x, bb * kBlock + (int64_t)t * E, rx);
+      if constexpr (OP == LIFT_OP_DOT) load_raw<DT, E>(y, bb * kBlock + (int64_t)t * E, ry);
+      fold_block<OP, DT, E>(acc, rx, ry, block_scale<OP, DT>(xs, ys, bb));
+    }
+    b = full * kBlock < n && (int64_t)blockIdx.x == full % G ? full : n;   // the ragged block
+  } else if constexpr (!GUARDED) {
     for (; b + (U - 1) * G < full; b += U * G) {
       Raw<DT, E> rx[U], ry[U];
       float sc[U];
@@ -260,14 +286,15 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-template <int OP, int DT, int THREADS, int U, bool GUARDED>
+template <int OP, int DT, int THREADS, int U, bool GUARDED, bool CONTIG = false>
 struct Mixed {
   static const void* kernel() {
-    return reinterpret_cast<const void*>(&mixed_reduce<OP, DT, THREADS, U, GUARDED>);
+    return reinterpret_cast<const void*>(&mixed_reduce<OP, DT, THREADS, U, GUARDED, CONTIG>);
   }
-  // persistent grid with the same number of blocks for every CTA
+  // persistent grid with the same number of blocks (super-blocks) for every CTA
   static int64_t grid(const Variant&, const Args& a) {
-    const int64_t nb = a.n > 0 ? (a.n + kBlock - 1) / kBlock : 1;
+    int64_t nb = a.n > 0 ? (a.n + kBlock - 1) / kBlock : 1;
+    if (CONTIG && nb >= U) nb /= U;
     const int64_t g = persistent_grid(kernel(), THREADS, 0, 1);
     if (g <= 0) return 0;
     const int64_t per = (nb + g - 1) / g;
@@ -293,9 +320,9 @@ struct Mixed {
   }
 };
 
-template <int OP, int DT, int THREADS, int U, bool GUARDED>
+template <int OP, int DT, int THREADS, int U, bool GUARDED, bool CONTIG = false>
 Variant mixed_variant(int opid, const char* name) {
-  using K = Mixed<OP, DT, THREADS, U, GUARDED>;
+  using K = Mixed<OP, DT, THREADS, U, GUARDED, CONTIG>;
   constexpr int E = kBlock / THREADS;
   Variant v{};
   v.info.op = opid;
@@ -337,6 +364,15 @@ void register_one(std::vector<Variant>& L, int opid, const char* tag) {
   L.push_back(mixed_variant<OP, DT, 64, 2, false>(opid, nm));
   snprintf(nm, sizeof nm, "%s_t64_u4", tag);
   L.push_back(mixed_variant<OP, DT, 64, 4, false>(opid, nm));
+  // a CTA step over U consecutive blocks (one contiguous run per step)
+  snprintf(nm, sizeof nm, "%s_t256_u4_c", tag);
+  L.push_back(mixed_variant<OP, DT, 256, 4, false, true>(opid, nm));
+  snprintf(nm, sizeof nm, "%s_t128_u4_c", tag);
+  L.push_back(mixed_variant<OP, DT, 128, 4, false, true>(opid, nm));
+  snprintf(nm, sizeof nm, "%s_t256_u8_c", tag);
+  L.push_back(mixed_variant<OP, DT, 256, 8, false, true>(opid, nm));
+  snprintf(nm, sizeof nm, "%s_t128_u2_c", tag);
+  L.push_back(mixed_variant<OP, DT, 128, 2, false, true>(opid, nm));
   for (size_t i = 0; i < L.size(); ++i) {
     L[i].info.id = static_cast<int>(i);
     L[i].fallback = guarded;
