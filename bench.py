@@ -11,8 +11,9 @@ pick's slowdown against an on-the-spot exhaustive sweep of each op.  The metric 
 its fraction of the measured HBM peak.  Inputs (3 x 256 MiB) exceed the
 129 MB L2, so no flush is needed between steps.
 
-Other workloads (``--workload``): asum (n = 2^20, L2 flushed before every
-step), gemv_square (8192 x 8192), gemv_tall (65536 x 1024), mixed (bf16 and
+Other workloads (``--workload``): asum (n = 2^20; each call reads the next of
+64 copies of x, twice the L2 in all, or with ``--submit eager`` the L2 is
+flushed before every step), gemv_square (8192 x 8192), gemv_tall (65536 x 1024), mixed (bf16 and
 fp8 asum / dot at 2^28), batch (20,000 ops), and more.  A default run (the
 dot/scal workload on one GPU) also measures asum, both gemv shapes, mixed
 and batch after the headline step, each with its own roofline, oracle check
@@ -282,6 +283,7 @@ def run_ours(args, rank, world, dist):
     graph_calls = []
     flushed = False  # True: an L2 flush runs between the timed spans of each step
     collect = None   # after the timed steps: the GPU results the oracle leg checks
+    pre_timed = None  # run once after the warm-up, before the timed region opens
 
     for name in args.variant or []:          # pin variants by name (profiling)
         for op in range(lift.NUM_OPS):
@@ -487,16 +489,39 @@ def run_ours(args, rank, world, dist):
         bytes_step = 4 * n
         kas = ["asum:" + pa["name"], 4 * n, [], []]
         kernels = [kas]
+        if args.submit == "graph":
+            # cold data without a flush inside the timed region: every call
+            # reads the next of ROT copies of x (ROT * 4 MiB = 256 MiB, twice
+            # the L2), so a copy is read again only after 252 MiB of other
+            # reads; the L2 is flushed once before the timed steps
+            ROT = 64
+            copies = x.repeat(ROT).view(ROT, n)
+            nxt = [0]
 
-        def step(timed):
-            flush.sum()     # read 512 MiB: evicts x from L2 and leaves no dirty lines
-            if timed:
-                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ev[0].record(s)
-            lift.lift_asum_v(va, x, n, r)
-            if timed:
-                ev[1].record(s)
-                kas[2].append(ev[0]); kas[3].append(ev[1])
+            def rotating():
+                lift.lift_asum_v(va, copies[nxt[0] % ROT], n, r)
+                nxt[0] += 1
+
+            graph_calls = [(kas, rotating)]
+
+            def step(timed):
+                if timed:
+                    ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev[0].record(s)
+                rotating()
+                if timed:
+                    ev[1].record(s)
+                    kas[2].append(ev[0]); kas[3].append(ev[1])
+        else:
+            def step(timed):
+                flush.sum()     # read 512 MiB: evicts x from L2 and leaves no dirty lines
+                if timed:
+                    ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev[0].record(s)
+                lift.lift_asum_v(va, x, n, r)
+                if timed:
+                    ev[1].record(s)
+                    kas[2].append(ev[0]); kas[3].append(ev[1])
 
         def e2e_step(xp, rp):
             x.copy_(xp, non_blocking=True)
@@ -506,9 +531,14 @@ def run_ours(args, rank, world, dist):
         host = dict(xp=torch.from_numpy(xh).pin_memory(), rp=torch.empty(1).pin_memory())
         collect = lambda: {"asum": float(r.item())}  # noqa: E731
         h2d, d2h = 4 * n, 4
-        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]],
-                  "l2": "flushed before every step (a 512 MiB read between the timed spans)"}
-        flushed = True
+        config = {"workload": WORKLOADS[wl]["desc"], "n": n, "variants": [pa["name"]]}
+        if args.submit == "graph":
+            config["l2"] = ("cold: every call reads the next of 64 copies of x (256 MiB in all, "
+                            "twice the L2); the L2 flushed once before the timed steps")
+            pre_timed = flush.sum
+        else:
+            config["l2"] = "flushed before every step (a 512 MiB read between the timed spans)"
+            flushed = True
     elif wl == "blackscholes":
         n = WORKLOADS[wl]["n"]
         sh = synth.stock_prices(n)
@@ -748,6 +778,8 @@ def run_ours(args, rank, world, dist):
             graphs["step"].replay()
         else:
             step(False)
+    if pre_timed is not None:
+        pre_timed()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
