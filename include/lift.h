@@ -39,7 +39,8 @@
  *  - The reductions use a per-device workspace allocated by lift_init
  *    (partials, ticket counters, a status word), one slot per stream for up
  *    to 8 streams of a device; calls on the same stream are ordered by it.
- *    Calls on more than 8 streams at once share slots and can race.
+ *    Calls on more than 8 streams at once share slots and can race (and
+ *    after 4096 distinct stream handles the assignment starts afresh).
  *  - lift_last_error() returns a detail message for the last failure of the
  *    calling thread.
  */
@@ -381,7 +382,8 @@ lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float*
  *                      size for scal, axpy, BlackScholes, gemv and gemv-T,
  *                      allocated and freed around the timing).  The fastest
  *                      is cached per (op, shape, alignment); the first such
- *                      call waits for the timing.  A call made while its
+ *                      call waits for the timing (one timing runs at a time;
+ *                      other threads' picks do not wait for it).  A call made while its
  *                      stream is being captured into a CUDA graph,
  *                      lift_pick and the batch never time: they use a
  *                      cached winner or the plain learned pick.  Loading

@@ -65,6 +65,9 @@ Workspace* stream_workspace(DeviceState* st, cudaStream_t stream) {
   auto key = std::make_pair(st, stream);
   auto it = g_slot_of.find(key);
   if (it == g_slot_of.end()) {
+    // a long-running process may see many short-lived streams: forget the
+    // assignments once there are many (slots are then dealt afresh)
+    if (g_slot_of.size() >= 4096) g_slot_of.clear();
     int& nx = g_next_slot[st];
     it = g_slot_of.emplace(key, nx).first;
     nx = (nx + 1) % kWsSlots;
@@ -406,7 +409,9 @@ struct TuneKey {
   }
 };
 static std::map<TuneKey, int> g_tuned;
-static int64_t g_tune_launches = 0;
+static std::atomic<int64_t> g_tune_launches{0};
+static std::mutex g_tune_mu;          // one timing at a time
+static uint64_t g_policy_gen = 0;     // bumped whenever a policy is loaded
 
 static bool in_box(int op, const Args& a) {
   const Box& b = g_mlp.box[op];
@@ -555,7 +560,7 @@ static int tune_candidates(int op, const Args& a0, const std::vector<int>& cand,
 }
 
 static int pick_variant(int op, const Args& a, cudaStream_t s = nullptr, bool may_tune = false) {
-  std::lock_guard<std::mutex> lk(g_policy_mu);
+  std::unique_lock<std::mutex> lk(g_policy_mu);
   if (g_override[op] >= 0) return g_override[op];
   int v = -1;
   if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < g_mlp.ops) v = mlp_pick(op, a);
@@ -583,9 +588,19 @@ static int pick_variant(int op, const Args& a, cudaStream_t s = nullptr, bool ma
         const int known = (op + 1 < g_mlp.ops ? g_mlp.offsets[op + 1] : g_mlp.V) - g_mlp.offsets[op];
         for (int i = known; i < (int)L.size(); ++i)      // newer than the model
           if (eligible(op, L[i], a)) add(i);
-        const int w = tune_candidates(op, a, cand, s);
+        // time without holding the policy lock (other threads keep picking);
+        // one timing at a time, and its winner kept only if the weights did
+        // not change meanwhile
+        const uint64_t gen = g_policy_gen;
+        lk.unlock();
+        int w = -1;
+        {
+          std::lock_guard<std::mutex> tk(g_tune_mu);
+          w = tune_candidates(op, a, cand, s);
+        }
+        lk.lock();
         if (w >= 0) {
-          g_tuned[key] = w;
+          if (g_policy_gen == gen) g_tuned[key] = w;
           v = w;
         }
       }
@@ -1217,6 +1232,7 @@ lift_status lift_set_policy(int policy, const char* path) {
     g_mlp = m;
     g_policy = policy;
     g_tuned.clear();
+    ++g_policy_gen;
     return LIFT_OK;
   }
   return set_error(LIFT_ERR_INVALID_ARG, "unknown policy");
@@ -1225,7 +1241,7 @@ lift_status lift_set_policy(int policy, const char* path) {
 lift_status lift_tune_stats(int64_t* tuned_shapes, int64_t* timed_launches) {
   std::lock_guard<std::mutex> lk(g_policy_mu);
   if (tuned_shapes) *tuned_shapes = (int64_t)g_tuned.size();
-  if (timed_launches) *timed_launches = g_tune_launches;
+  if (timed_launches) *timed_launches = g_tune_launches.load();
   return LIFT_OK;
 }
 
