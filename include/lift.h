@@ -391,7 +391,10 @@ lift_status lift_dot_ex_v(int variant, lift_dtype t, const void* x, const float*
  * Both learned policies choose only among the variants that run as
  * themselves on the call's arguments (vector loads need the pointers and,
  * for gemv and gemv-T, the row pitch aligned to the vector width); an
- * explicit or FIXED variant that cannot runs its guarded fallback.
+ * explicit or FIXED variant that cannot runs its guarded fallback.  Their
+ * picks are memoised per (op, shape, pointer and pitch alignment), so a
+ * repeated call shape costs a table lookup; loading weights clears the
+ * memo.
  * ------------------------------------------------------------------------ */
 typedef enum {
   LIFT_POLICY_FIXED = 0,

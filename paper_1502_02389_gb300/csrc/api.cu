@@ -403,12 +403,14 @@ constexpr double kBoxSlack = 0.1;      // log2 units beyond the trained range st
 struct TuneKey {
   int op;
   int64_t n, M, N;
-  int align;   // which of the op's variants run as themselves (their eligibility bits)
+  uint64_t align;   // alignment_signature: which of the op's variants run as themselves
   bool operator<(const TuneKey& o) const {
     return std::tie(op, n, M, N, align) < std::tie(o.op, o.n, o.M, o.N, o.align);
   }
 };
 static std::map<TuneKey, int> g_tuned;
+static std::map<TuneKey, int> g_picked;    // learned picks, memoised per call shape
+constexpr size_t kPickCacheMax = 1 << 16;
 static std::atomic<int64_t> g_tune_launches{0};
 static std::mutex g_tune_mu;          // one timing at a time
 static uint64_t g_policy_gen = 0;     // bumped whenever a policy is loaded
@@ -441,14 +443,16 @@ static double input_bytes(int op, const Args& a) {
   }
 }
 
-static int eligibility_bits(int op, const Args& a) {
-  const auto& L = registry(op);
-  int bits = 0, k = 0;
-  for (const auto& v : L) {
-    if (eligible(op, v, a)) bits |= 1 << (k % 30);
-    ++k;
-  }
-  return bits;
+// What decides which variants run as themselves (see eligible): the
+// pointers' residues modulo 32 bytes (the widest vector), and for the
+// matrices the row pitch and width residues modulo 256 elements.
+static uint64_t alignment_signature(int op, const Args& a) {
+  auto r = [](const void* p) { return (uint64_t)(reinterpret_cast<uintptr_t>(p) % 32); };
+  uint64_t sig = r(a.x) | r(a.y) << 5 | r(a.A) << 10 | r(a.out) << 15;
+  if (op == LIFT_OP_BLACKSCHOLES) sig |= r(a.result) << 20;
+  if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T)
+    sig |= (uint64_t)(a.lda % 256) << 25 | (uint64_t)(a.N % 256) << 33 | (uint64_t)(a.N > 0) << 41;
+  return sig;
 }
 
 static double l2_bytes() {
@@ -563,20 +567,33 @@ static int pick_variant(int op, const Args& a, cudaStream_t s = nullptr, bool ma
   std::unique_lock<std::mutex> lk(g_policy_mu);
   if (g_override[op] >= 0) return g_override[op];
   int v = -1;
-  if (g_policy == LIFT_POLICY_MLP && g_mlp.V > 0 && op < g_mlp.ops) v = mlp_pick(op, a);
-  if (g_policy == LIFT_POLICY_MLP_TUNE && g_mlp.V > 0 && op < g_mlp.ops) {
+  const bool learned = (g_policy == LIFT_POLICY_MLP || g_policy == LIFT_POLICY_MLP_TUNE) &&
+                       g_mlp.V > 0 && op < g_mlp.ops;
+  const bool matrix = op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T;   // shape = (M, N)
+  const TuneKey key{op, matrix ? 0 : a.n, a.M, a.N, learned ? alignment_signature(op, a) : 0};
+  if (learned) {
+    auto it = g_tuned.find(key);              // a timed winner (MLP_TUNE)
+    if (g_policy == LIFT_POLICY_MLP_TUNE && it != g_tuned.end()) return it->second;
+    auto jt = g_picked.find(key);             // a pick made before for this shape
+    if (jt != g_picked.end()) return jt->second;
+  }
+  auto memo = [&](int w) {
+    if (g_picked.size() >= kPickCacheMax) g_picked.clear();
+    g_picked[key] = w;
+  };
+  if (g_policy == LIFT_POLICY_MLP && learned) {
+    v = mlp_pick(op, a);
+    if (v >= 0) memo(v);
+  }
+  if (g_policy == LIFT_POLICY_MLP_TUNE && learned) {
     const auto r = mlp_rank(op, a);
     if (!r.empty()) {
       v = r[0].second;
-      const bool matrix = op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T;   // shape = (M, N)
-      const TuneKey key{op, matrix ? 0 : a.n, a.M, a.N, eligibility_bits(op, a)};
-      auto it = g_tuned.find(key);
-      if (it != g_tuned.end()) {
-        v = it->second;
-      } else if (may_tune &&
-                 (!in_box(op, a) || (r.size() > 1 && r[1].first - r[0].first < kTuneMargin &&
-                                     input_bytes(op, a) >= 2.0 * l2_bytes())) &&
-                 !capturing(s)) {
+      const bool unsure = !in_box(op, a) || (r.size() > 1 && r[1].first - r[0].first < kTuneMargin &&
+                                             input_bytes(op, a) >= 2.0 * l2_bytes());
+      if (!unsure) {
+        memo(v);                               // no timing will ever be wanted here
+      } else if (may_tune && !capturing(s)) {
         std::vector<int> cand;
         auto add = [&](int c) {
           if (c >= 0 && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
@@ -1232,6 +1249,7 @@ lift_status lift_set_policy(int policy, const char* path) {
     g_mlp = m;
     g_policy = policy;
     g_tuned.clear();
+    g_picked.clear();
     ++g_policy_gen;
     return LIFT_OK;
   }

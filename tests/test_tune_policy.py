@@ -52,3 +52,31 @@ def test_box_parsing(L, tmp_path, tail, ok):
             L.lift_set_policy(L.POLICY_MLP_TUNE, str(p))
         assert e.value.status == L.ERR_INVALID_ARG
     L.lift_set_policy(L.POLICY_FIXED)
+
+
+def test_memoised_picks_follow_reloaded_weights(L, tmp_path):
+    # picks are memoised per call shape; loading other weights must not
+    # return the memo of the previous ones
+    lines = open(costmodel.WEIGHTS).read().split("\n")
+    head = lines[0].split()
+    d_in, h1, h2, V = (int(v) for v in head[2:6])
+    off = [int(v) for v in lines[1].split()[2:]]
+    params = [float(v) for v in lines[2].split()]
+    n_before_b3 = d_in * h1 + h1 + h1 * h2 + h2 + h2 * V
+    for shape in ((L.OP_DOT, 1 << 26, 0, 0), (L.OP_ASUM, 1 << 22, 0, 0)):
+        op = shape[0]
+        L.lift_set_policy(L.POLICY_MLP, costmodel.WEIGHTS)
+        first = L.lift_pick(*shape)
+        assert L.lift_pick(*shape) == first                 # memoised, same answer
+        other = 0 if first != 0 else 1
+        p2 = list(params)
+        p2[n_before_b3 + off[op] + other] -= 1000.0         # make `other` predicted fastest
+        lines2 = list(lines)
+        lines2[2] = " ".join(f"{v:.9g}" for v in p2)
+        w2 = tmp_path / f"w{op}.txt"
+        w2.write_text("\n".join(lines2))
+        L.lift_set_policy(L.POLICY_MLP, str(w2))
+        assert L.lift_pick(*shape) == other
+        L.lift_set_policy(L.POLICY_MLP, costmodel.WEIGHTS)
+        assert L.lift_pick(*shape) == first
+    L.lift_set_policy(L.POLICY_FIXED)
