@@ -252,9 +252,9 @@ static std::mutex g_policy_mu;
 // Variant names; looked up at first use.
 static const char* kDefaultName[LIFT_NUM_OPS] = {
     "asum_t4096_v4_ldg_p2", "dot_t4096_v4_ldg_p2", "scal_t2048_v4_ldg_pertile",
-    "gemv_tma_w4_c1024_s3", "asum_bf16_t256_u4", "dot_bf16_t256_u8", "asum_fp8_t256_u4",
-    "dot_fp8_t256_u4", "nrm2_t4096_v4_ldg_p2", "sum_t4096_v4_ldg_p2", "axpy_t2048_v4_ldg_pertile",
-    "gemv_t_t256_v4_u4_p2", "blackscholes_t128_v4_u4_fast_pertile", "asum_comp_t256_v4_u4",
+    "gemv_tma_w4_c1024_s3", "asum_bf16_t256_u4", "dot_bf16_t256_u4", "asum_fp8_t256_u8_c",
+    "dot_fp8_t128_u2", "nrm2_t4096_v4_ldg_p2", "sum_t4096_v4_ldg_p2", "axpy_t2048_v4_ldg_pertile",
+    "gemv_t_t128_v4_u8_p2", "blackscholes_t128_v4_u4_fast_pertile", "asum_comp_t256_v4_u4",
     "dot_comp_t256_v4_u4"};
 
 static int find_variant(int op, const char* name) {
