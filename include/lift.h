@@ -193,8 +193,14 @@ lift_status lift_axpy_v(int variant, int64_t n, float alpha, const float* x, flo
  * halving tree over the lanes (two-pass variants, a second kernel); then
  * z_j = fl(alpha * sum), y_j = fl(z_j + fl(beta * y_j)).  M == 0 gives
  * y <- beta * y.  Uses the lift_init workspace (RB * N partial slots and,
- * one pass, one counter per column block).  Errors: LIFT_ERR_UNSUPPORTED
- * when RB * N exceeds the workspace.
+ * one pass, one counter per column block).  The staged variants (info
+ * stages > 0) copy row segments into shared memory with bulk copies and
+ * give the two-pass variants' bits for the same blocks; they run as
+ * themselves when A and x are 16-byte aligned and N and lda are multiples
+ * of 4, and a call that is not runs the 4-byte-load variant 0 instead.
+ * Errors: LIFT_ERR_UNSUPPORTED when RB * N exceeds the workspace; a staged
+ * copy wait that runs out records LIFT_ERR_TIMEOUT in the status word
+ * (lift_read_status) and leaves the affected y_j NaN.
  * lift_gemv_t_blocks reports the rows per block and the number of blocks a
  * variant uses for an M x N call.
  * ------------------------------------------------------------------------ */

@@ -59,7 +59,8 @@ def runs_as_itself(op: int, variant: int, N: int) -> bool:
     """Whether a variant runs as itself (not its guarded fallback) on a dense
     call with aligned pointers: gemv and gemv-T rows of N floats must be a
     whole number of the variant's vectors (and of 16-byte granules for the
-    bulk-copy gemv).  The same test the library's learned picks apply."""
+    bulk-copy gemv and gemv-T).  The same test the library's learned picks
+    apply."""
     if op not in (lift.OP_GEMV, lift.OP_GEMV_T):
         return True
     d = lift.lift_variant_describe(op, variant)
@@ -67,7 +68,7 @@ def runs_as_itself(op: int, variant: int, N: int) -> bool:
         return False
     if op == lift.OP_GEMV and d["tree"] == 3 and N % 256 != 0:     # tensor-copy staging
         return False
-    return not (op == lift.OP_GEMV and d["stages"] > 0 and (N == 0 or N % 4 != 0))
+    return not (d["stages"] > 0 and (N == 0 or N % 4 != 0))
 
 
 def dataset(records: List[Dict], off: Optional[List[int]] = None, V: Optional[int] = None):

@@ -254,7 +254,7 @@ static const char* kDefaultName[LIFT_NUM_OPS] = {
     "asum_t4096_v4_ldg_p2", "dot_t4096_v4_ldg_p2", "scal_t2048_v4_ldg_pertile",
     "gemv_tma_w4_c1024_s3", "asum_bf16_t256_u4", "dot_bf16_t256_u4", "asum_fp8_t256_u8_c",
     "dot_fp8_t128_u2", "nrm2_t4096_v4_ldg_p2", "sum_t4096_v4_ldg_p2", "axpy_t2048_v4_ldg_pertile",
-    "gemv_t_t128_v4_u8_p2", "blackscholes_t128_v4_u4_fast_pertile", "asum_comp_t256_v4_u4",
+    "gemv_t_t128_v4_r16_s3", "blackscholes_t128_v4_u4_fast_pertile", "asum_comp_t256_v4_u4",
     "dot_comp_t256_v4_u4"};
 
 static int find_variant(int op, const char* name) {
@@ -301,14 +301,15 @@ static bool ptr_ok(const void* p, int bytes) { return p == nullptr || aligned(p,
 
 // Whether variant v runs as itself on these arguments: its vector loads need
 // the pointers (and, gemv and gemv-T, the row pitch) aligned to its vector
-// width, and the bulk-copy gemv needs whole 16-byte row granules.  Otherwise
+// width, and the bulk-copy gemv and gemv-T need whole 16-byte row granules.  Otherwise
 // the library runs the variant's guarded fallback instead.
 static bool eligible(int op, const Variant& v, const Args& a) {
   const int al = v.align_bytes;
   bool ok = ptr_ok(a.x, al) && ptr_ok(a.y, al) && ptr_ok(a.A, al) && ptr_ok(a.out, al);
   if (op == LIFT_OP_BLACKSCHOLES) ok = ok && ptr_ok(a.result, al);   // the put array
   if (op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) ok = ok && ((a.lda * 4) % al == 0);
-  if (op == LIFT_OP_GEMV && v.info.stages > 0) ok = ok && a.N > 0 && a.N % 4 == 0;
+  if ((op == LIFT_OP_GEMV || op == LIFT_OP_GEMV_T) && v.info.stages > 0)
+    ok = ok && a.N > 0 && a.N % 4 == 0;
   // tensor copies: whole 256-float runs per row, 16-byte row strides
   if (op == LIFT_OP_GEMV && v.info.tree == 3) ok = ok && a.N % 256 == 0 && a.lda % 4 == 0;
   return ok;

@@ -275,6 +275,163 @@ __global__ void __launch_bounds__(THREADS)
   if (threadIdx.x == 0) *ticket = 0u;           // ready for the next call
 }
 
+// Staged form (the toLocal lowering of Fig. 4d applied to the column
+// block's rows): the same expression and blocks as the two-pass kernel --
+// per column, the block's rows in groups of 32 folded in row order from
+// zero, the group sums added with Neumaier's compensated step, one partial
+// per (column, block) written column-major for gemv_t_combine -- so both
+// give the same bits.  Only the movement of A differs: one producer warp
+// streams the block's rows, R at a time, into a ring of S shared-memory
+// stages with one bulk copy per row segment (cw = min(CB, N - first
+// column) floats, contiguous in A), a full mbarrier per stage counting the
+// bytes in and an empty mbarrier counting the consumer warps that have read
+// it; consumer thread t folds column quads t, t + THREADS, ... of every
+// staged row (a warp reads 512 contiguous bytes of shared memory per quad).
+// The copy engine moves whole row segments of 2-8 KB, where the direct
+// kernel's warps each issue 512-byte pieces of rows lda apart.  Requires A
+// and x 16-byte aligned and N, lda multiples of 4; R divides 32 so that no
+// stage straddles a group.  A wait that runs out (the limit set with
+// lift_set_wait_polls) records LIFT_ERR_TIMEOUT: a consumer warp stops as a
+// whole and writes NaN partials, and the side that stops waits, with the
+// full limit, for every copy that may still be in flight into the ring, so
+// none lands after the CTA has left.
+template <int THREADS, int VW, int R, int S>
+__global__ void __launch_bounds__(THREADS + kWarp, 1)
+    gemv_t_staged(int64_t M, int64_t N, const float* __restrict__ A, int64_t lda,
+                  const float* __restrict__ x, int64_t B, float* __restrict__ partials,
+                  int* status, uint32_t polls) {
+  constexpr int CB = THREADS * VW, Q = VW / 4, WARPS = THREADS / kWarp;
+  static_assert(VW % 4 == 0 && kGroupRows % R == 0 && R % 4 == 0, "quads; stages within groups");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  const int64_t cb = blockIdx.x, rb = blockIdx.y, RB = gridDim.y;
+  const int64_t col0 = cb * CB;
+  const int64_t cw = N - col0 < CB ? N - col0 : CB;
+  const int64_t r0 = rb * B, r1 = (r0 + B < M) ? r0 + B : M;
+  const int64_t steps = r1 > r0 ? (r1 - r0 + R - 1) / R : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], WARPS);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (threadIdx.x >= THREADS) {
+    // producer warp: one lane streams the block's row segments into the ring
+    if (threadIdx.x == THREADS) {
+      const uint32_t bytes = static_cast<uint32_t>(cw * sizeof(float));
+      for (int64_t k = 0; k < steps; ++k) {
+        const int s = static_cast<int>(k % S);
+        if (k >= S && !mbar_wait(&empty_bar[s], static_cast<uint32_t>(((k / S) - 1) & 1), polls)) {
+          report(status, LIFT_ERR_TIMEOUT);
+          for (int64_t q = k - S; q < k; ++q)       // steps whose copies may be in flight
+            mbar_wait(&full_bar[q % S], static_cast<uint32_t>((q / S) & 1));
+          return;
+        }
+        const int64_t i0 = r0 + k * R;
+        const int rows = static_cast<int>(r1 - i0 < R ? r1 - i0 : R);
+        float* st = buf + (size_t)s * R * CB;
+        mbar_arrive_expect_tx(&full_bar[s], rows * bytes);
+        for (int r = 0; r < rows; ++r)
+          bulk_g2s(st + r * CB, A + (i0 + r) * lda + col0, bytes, &full_bar[s]);
+      }
+    }
+    return;
+  }
+
+  const int lane = threadIdx.x & (kWarp - 1);
+  float acc[VW], cmp[VW], gs[VW];
+#pragma unroll
+  for (int l = 0; l < VW; ++l) acc[l] = cmp[l] = gs[l] = 0.f;
+  bool failed = false;
+  for (int64_t k = 0; k < steps; ++k) {
+    const int s = static_cast<int>(k % S);
+    if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[s], static_cast<uint32_t>((k / S) & 1), polls))) {
+      // the producer issues no step past k + S - 1 before this warp's
+      // arrival for step k, which never comes
+      if (threadIdx.x == 0) {
+        report(status, LIFT_ERR_TIMEOUT);
+        for (int64_t q = k; q < k + S && q < steps; ++q)
+          mbar_wait(&full_bar[q % S], static_cast<uint32_t>((q / S) & 1));
+      }
+      failed = true;
+      break;
+    }
+    const int64_t i0 = r0 + k * R;
+    const float* st = buf + (size_t)s * R * CB;
+    if (i0 + R <= r1) {
+      float xv[R];
+#pragma unroll
+      for (int u = 0; u < R; u += 4) {          // i0 is a multiple of 4, x 16-byte aligned
+        const float4 q = __ldg(reinterpret_cast<const float4*>(x + i0 + u));
+        xv[u] = q.x;
+        xv[u + 1] = q.y;
+        xv[u + 2] = q.z;
+        xv[u + 3] = q.w;
+      }
+#pragma unroll
+      for (int qd = 0; qd < Q; ++qd) {
+        const int c = (qd * THREADS + threadIdx.x) * 4;
+        if (c < cw) {
+          Vec<4> a[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) ld_smem<4>(st + r * CB + c, a[r]);
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+              gs[qd * 4 + l] = __fadd_rn(gs[qd * 4 + l], __fmul_rn(a[r].v[l], xv[r]));
+        }
+      }
+    } else {
+      const int rows = static_cast<int>(r1 - i0);
+      for (int r = 0; r < rows; ++r) {
+        const float xr = __ldg(x + i0 + r);
+#pragma unroll
+        for (int qd = 0; qd < Q; ++qd) {
+          const int c = (qd * THREADS + threadIdx.x) * 4;
+          if (c < cw) {
+            Vec<4> a;
+            ld_smem<4>(st + r * CB + c, a);
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+              gs[qd * 4 + l] = __fadd_rn(gs[qd * 4 + l], __fmul_rn(a.v[l], xr));
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty_bar[s]))
+                   : "memory");
+    // a group of 32 rows ends here, or the block does
+    if (((k + 1) * R) % kGroupRows == 0 || k + 1 == steps) {
+#pragma unroll
+      for (int l = 0; l < VW; ++l) {
+        neumaier_add(acc[l], cmp[l], gs[l]);
+        gs[l] = 0.f;
+      }
+    }
+  }
+  // the combine kernel may start launching; it waits for this grid to end
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#pragma unroll
+  for (int qd = 0; qd < Q; ++qd) {
+    const int64_t c = (qd * THREADS + threadIdx.x) * 4;
+    if (c < cw) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        partials[(col0 + c + l) * RB + rb] =
+            failed ? __int_as_float(0x7fc00000) : neumaier_value(acc[qd * 4 + l], cmp[qd * 4 + l]);
+    }
+  }
+}
+
 constexpr int kCombineThreads = 256;
 constexpr int64_t kMaxRowBlocks2 = 512;   // two pass: at most 16 partials per lane
 
@@ -396,6 +553,61 @@ struct GemvTCluster {
   }
 };
 
+template <int THREADS, int VW, int R, int S>
+struct GemvTStaged {
+  static constexpr int CB = THREADS * VW;
+  static const void* kernel() {
+    return reinterpret_cast<const void*>(&gemv_t_staged<THREADS, VW, R, S>);
+  }
+  static size_t smem() { return (size_t)S * R * CB * sizeof(float); }
+  // at most one wave of the persistent size (row blocks rounded down: with
+  // two to four CTAs per SM a second, nearly empty wave costs a whole
+  // block's time), within the partials workspace and kMaxRowBlocks2 row
+  // blocks
+  static void shape(const Args& a, int64_t& ncb, int64_t& RB, int64_t& B) {
+    ncb = (a.N + CB - 1) / CB;
+    const int64_t g = persistent_grid(kernel(), THREADS + kWarp, smem(), 1);
+    int64_t want = g > ncb ? g / ncb : 1;
+    DeviceState* st = current_state();
+    const int64_t cap = st ? st->ws.capacity / (a.N > 0 ? a.N : 1) : 1;
+    if (want > cap) want = cap;
+    if (want > kMaxRowBlocks2) want = kMaxRowBlocks2;
+    if (want > a.M) want = a.M;
+    if (want < 1) want = 1;
+    B = (a.M + want - 1) / want;
+    B = (B + kBlockAlign - 1) / kBlockAlign * kBlockAlign;
+    RB = (a.M + B - 1) / B;
+  }
+  static int64_t grid(const Variant&, const Args& a) {
+    int64_t ncb, RB, B;
+    shape(a, ncb, RB, B);
+    return ncb * RB;
+  }
+  static lift_status launch(const Variant& v, const Args& a, cudaStream_t s) {
+    DeviceState* st = current_state();
+    if (a.N == 0) return LIFT_OK;
+    if (a.M == 0) return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t with M == 0 goes through gemv_t_scale");
+    if (a.N % 4 != 0 || a.lda % 4 != 0 || !aligned(a.A, 16) || !aligned(a.x, 16))
+      return set_error(LIFT_ERR_UNSUPPORTED, "staged gemv_t: N, lda, A or x not in 16-byte granules");
+    int64_t ncb, RB, B;
+    shape(a, ncb, RB, B);
+    if (RB * a.N > st->ws.capacity)
+      return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: N exceeds the partials workspace");
+    if (RB > 65535) return set_error(LIFT_ERR_UNSUPPORTED, "gemv_t: too many row blocks");
+    int64_t M = a.M, N = a.N, lda = a.lda;
+    const float* A = a.A;
+    const float* x = static_cast<const float*>(a.x);
+    float* partials = a.ws->partials;
+    int* status = a.ws->status;
+    uint32_t polls = wait_polls();
+    void* args[] = {&M, &N, &A, &lda, &x, &B, &partials, &status, &polls};
+    lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS + kWarp),
+                                  smem(), 1, s, args);
+    if (r != LIFT_OK) return r;
+    return launch_rows_combine(N, RB, a.alpha, a.beta, partials, a.out, s);
+  }
+};
+
 // M == 0: every column's dot is the empty sum, y <- fl(beta * y) (0 if beta == 0)
 __global__ void gemv_t_scale(int64_t N, float beta, float* y) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
@@ -477,6 +689,30 @@ lift_status gemv_t_empty_rows(int64_t N, float beta, float* y, cudaStream_t s) {
   X(128, 8, 4, 8, "t128_v8_u4_c8")      \
   X(64, 4, 8, 8, "t64_v4_u8_c8")
 
+// staged forms (appended after the cluster forms): THREADS consumer threads,
+// VW columns each, R rows per stage, S stages (16-32 KB stages, two to four
+// CTAs per SM)
+#define LIFT_GEMV_T_STAGED_VARIANTS(X) \
+  X(64, 4, 32, 3, "t64_v4_r32_s3")     \
+  X(128, 4, 16, 3, "t128_v4_r16_s3")   \
+  X(128, 4, 16, 2, "t128_v4_r16_s2")   \
+  X(128, 4, 8, 3, "t128_v4_r8_s3")     \
+  X(32, 4, 32, 3, "t32_v4_r32_s3")     \
+  X(64, 4, 16, 3, "t64_v4_r16_s3")
+
+template <int THREADS, int VW, int R, int S>
+Variant gemv_t_staged_variant(const char* name) {
+  using K = GemvTStaged<THREADS, VW, R, S>;
+  Variant v = gemv_t_variant<THREADS, VW, 1, 2>(name);
+  v.info.threads = THREADS + kWarp;
+  v.info.rows = R;
+  v.info.stages = S;
+  v.launch = &K::launch;
+  v.grid = &K::grid;
+  v.align_bytes = 16;
+  return v;
+}
+
 template <int THREADS, int VW, int U, int CL>
 Variant gemv_t_cluster_variant(const char* name) {
   using K = GemvTCluster<THREADS, VW, U, CL>;
@@ -499,6 +735,10 @@ void gemv_t_shape(int id, const Args& a, int64_t* B, int64_t* RB) {
   if (k++ == id) GemvTCluster<T, V, U, CL>::shape(a, ncb, rb, b);
   LIFT_GEMV_T_CLUSTER_VARIANTS(X)
 #undef X
+#define X(T, V, R, S, NAME) \
+  if (k++ == id) GemvTStaged<T, V, R, S>::shape(a, ncb, rb, b);
+  LIFT_GEMV_T_STAGED_VARIANTS(X)
+#undef X
   *B = b;
   *RB = rb;
 }
@@ -509,6 +749,9 @@ void register_gemv_t(std::vector<Variant>& L) {
 #undef X
 #define X(T, V, U, CL, NAME) L.push_back(gemv_t_cluster_variant<T, V, U, CL>(NAME));
   LIFT_GEMV_T_CLUSTER_VARIANTS(X)
+#undef X
+#define X(T, V, R, S, NAME) L.push_back(gemv_t_staged_variant<T, V, R, S>(NAME));
+  LIFT_GEMV_T_STAGED_VARIANTS(X)
 #undef X
   for (size_t i = 0; i < L.size(); ++i) L[i].info.id = static_cast<int>(i);
 }

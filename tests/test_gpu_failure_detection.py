@@ -123,3 +123,39 @@ def test_wait_polls_arguments(L):
     with pytest.raises(L.LiftError):
         L.lift_set_wait_polls((1 << 22) + 1)
     L.lift_set_wait_polls(1 << 22)
+
+
+def test_staged_gemv_t_timeout(L):
+    """The staged gemv-T forms driven down their timeout path: with the wait
+    limit at 0 the consumer warps give up on their first stage and the
+    producer on its first reuse of a stage; both wait (with the full limit)
+    for the copies in flight, the partials are NaN, so every y_j is NaN and
+    the status word reads LIFT_ERR_TIMEOUT.  With the limit restored the same
+    calls match the two-pass expression bit for bit."""
+    from oracle import lowlevel as ll
+    from oracle.patterns import evaluate
+    assert L.lift_read_status(1) == 0
+    M, N = 3000, 1100                     # several stages per block, a ragged column block
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((M, N)).astype(np.float32)
+    x = rng.standard_normal(M).astype(np.float32)
+    Ad, xd = torch.from_numpy(A).cuda(), torch.from_numpy(x).cuda()
+    staged = [v for v in L.variants(L.OP_GEMV_T) if v["stages"] > 0]
+    assert staged
+    L.lift_set_wait_polls(0)
+    try:
+        for v in staged:
+            yd = torch.zeros(N, device="cuda")
+            L.lift_gemv_t_v(v["id"], M, N, 1.0, Ad, N, xd, 0.0, yd)
+            torch.cuda.synchronize()
+            assert torch.isnan(yd).all().item(), v["name"]
+    finally:
+        L.lift_set_wait_polls(1 << 22)
+    assert L.lift_read_status(1) == L.ERR_TIMEOUT
+    for v in staged:
+        B, RB = L.lift_gemv_t_blocks(v["id"], M, N)
+        z = evaluate(ll.gemv_t_z_variant(M, N, 1.0, B, RB, 2), A, mode="f32", env={"x": x})
+        yd = torch.zeros(N, device="cuda")
+        L.lift_gemv_t_v(v["id"], M, N, 1.0, Ad, N, xd, 0.0, yd)
+        assert np.array_equal(yd.cpu().numpy(), z.astype(np.float32)), v["name"]
+    assert L.lift_read_status(1) == 0
