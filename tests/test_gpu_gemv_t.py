@@ -88,3 +88,42 @@ def test_edge_cases(L):
     L.lift_gemv_t(M, N, 1.0, dev(A), lda, dev(x), 0.0, yd)
     ref = A[:, :N].astype(np.float64).sum(axis=0)
     assert np.allclose(yd.cpu().numpy(), ref, rtol=0, atol=1e-4)
+
+
+@pytest.mark.parametrize("M,N", [(300, 1028), (4099, 96)])
+def test_padded_pitch_and_offsets(L, M, N):
+    """Rows lda = N + 4 apart with NaN in the padding (the staged forms copy
+    only the N floats of each row segment), and A, x 4 bytes off a 16-byte
+    boundary (every vector variant runs its fallback then): bit for bit
+    against each variant's expression on the unpadded matrix."""
+    rng = np.random.default_rng(M * 7 + N)
+    lda = N + 4
+    A = rng.standard_normal((M, N)).astype(np.float32)
+    Ap = np.full((M, lda), np.nan, np.float32)
+    Ap[:, :N] = A
+    x = rng.standard_normal(M).astype(np.float32)
+    y = rng.standard_normal(N).astype(np.float32)
+    for vid in range(L.lift_variant_count(L.OP_GEMV_T)):
+        info = L.lift_variant_describe(L.OP_GEMV_T, vid)
+        for offset in (0, 1):
+            # the library's rule: A, x (and y) and the pitch aligned to the
+            # variant's vectors (16 bytes for the staged copies, which also
+            # need N % 4 == 0); otherwise the 4-byte-load variant 0 runs
+            al = 16 if info["stages"] > 0 else 4 * info["vw"]
+            ok = (offset == 0 or al <= 4) and (lda * 4) % al == 0 and \
+                (info["stages"] == 0 or N % 4 == 0)
+            run = vid if ok else 0
+            B, RB = L.lift_gemv_t_blocks(run, M, N)
+            rinfo = L.lift_variant_describe(L.OP_GEMV_T, run)
+            z = evaluate(ll.gemv_t_z_variant(M, N, 0.75, B, RB, rinfo["passes"], rinfo["cluster"]), A,
+                         mode="f32", env={"x": x})
+            exp = evaluate(C(Map(add), Zip()), (z, evaluate(Map(mult_by(0.5)), y, mode="f32")),
+                           mode="f32").astype(np.float32)
+            Abuf = torch.zeros(M * lda + 8, device="cuda")
+            Abuf[offset:offset + M * lda] = dev(Ap.reshape(-1))
+            xbuf = torch.zeros(M + 8, device="cuda")
+            xbuf[offset:offset + M] = dev(x)
+            yd = dev(y)
+            L.lift_gemv_t_v(vid, M, N, 0.75, Abuf.data_ptr() + 4 * offset, lda,
+                            xbuf.data_ptr() + 4 * offset, 0.5, yd)
+            assert np.array_equal(yd.cpu().numpy(), exp), (info["name"], offset)
