@@ -15,9 +15,10 @@ Other workloads (``--workload``): asum (n = 2^20; each call reads the next of
 64 copies of x, twice the L2 in all, or with ``--submit eager`` the L2 is
 flushed before every step), gemv_square (8192 x 8192), gemv_tall (65536 x 1024), mixed (bf16 and
 fp8 asum / dot at 2^28), batch (20,000 ops), and more.  A default run (the
-dot/scal workload on one GPU) also measures asum, both gemv shapes, mixed
-and batch after the headline step, each with its own roofline, oracle check
-and CPU baseline, under ``config.sub`` (``--no-sub`` skips them).
+dot/scal workload on one GPU) also measures asum, both gemv shapes, mixed,
+batch, both gemv-T shapes and BlackScholes after the headline step, each
+with its own roofline, oracle check and CPU baseline, under ``config.sub``
+(``--no-sub`` skips them).
 
 Workloads whose step is a few plain calls (dot/scal, asum_large, gemv,
 gemv-T, mixed, BlackScholes) submit their K timed steps as one CUDA graph
@@ -1226,7 +1227,8 @@ METRIC = "HBM GB/s (frac of peak) for asum/dot/gemv; learned vs autotuned varian
 # the other configurations of the metric, measured in the same run after the
 # headline step: asum at 2^20 (L2 flushed), both gemv shapes, the bf16 and fp8
 # ops at 2^28, and the 20,000-op batched launch
-SUB_WORKLOADS = ("asum", "gemv_square", "gemv_tall", "mixed", "batch")
+SUB_WORKLOADS = ("asum", "gemv_square", "gemv_tall", "mixed", "batch", "gemv_t_square", "gemv_t_tall",
+                 "blackscholes")
 
 
 def run_subs(args, rank):
