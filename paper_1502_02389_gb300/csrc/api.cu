@@ -85,7 +85,13 @@ static void free_slots(DeviceState* st) {
   }
 }
 
+// Serialises whole initialisations, so two threads that call lift_init for
+// the same device at once set it up once (g_mu is held only around the
+// table, not across the allocations).
+static std::mutex g_init_mu;
+
 static lift_status init_device(int device) {
+  std::lock_guard<std::mutex> init_lk(g_init_mu);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_states.count(device)) return LIFT_OK;
@@ -733,6 +739,7 @@ lift_status lift_init(int device) {
 
 lift_status lift_finalize(void) {
   noalloc_forget();
+  std::lock_guard<std::mutex> init_lk(g_init_mu);
   std::lock_guard<std::mutex> lk(g_mu);
   int prev = -1;
   cudaGetDevice(&prev);
