@@ -130,6 +130,8 @@ template <int THREADS, int VW, int U, int CND>
 __global__ void __launch_bounds__(THREADS)
     bs_map(int64_t n, const float* __restrict__ s, float* __restrict__ call,
            float* __restrict__ put, BsConst c) {
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the previous kernel on the stream has completed
   const int64_t nv = n / VW;                         // whole vectors
   const int64_t stride = (int64_t)gridDim.x * THREADS * U;
   for (int64_t base = (int64_t)blockIdx.x * THREADS * U + threadIdx.x; base < nv; base += stride) {
@@ -189,7 +191,7 @@ struct BlackScholes {
     float* call = a.out;
     float* put = a.result;
     void* args[] = {&n, &prices, &call, &put, &c};
-    return launch_config(kernel(), dim3((unsigned)grid(v, a)), dim3(THREADS), 0, 1, s, args);
+    return launch_config(kernel(), dim3((unsigned)grid(v, a)), dim3(THREADS), 0, 1, s, args, true);
   }
 };
 

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(THREADS)
     comp_reduce(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
                 double* __restrict__ partials, unsigned* ticket, float* result, double* result64) {
   constexpr int64_t kTile = (int64_t)THREADS * VW * U;
+  pdl_wait();      // the previous kernel on the stream has completed
   const int t = threadIdx.x;
   const int64_t G = gridDim.x;
   const int64_t full = n / kTile;
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(THREADS)
       fold_vec<OP, VW>(acc, a, b);
     }
   }
+  pdl_trigger();   // streaming done: the next call's first kernel may be scheduled
   Comp c = acc[0];
 #pragma unroll
   for (int l = 1; l < VW; ++l) c = comp_merge(c, acc[l]);
@@ -122,7 +124,7 @@ struct CompReduce {
     float* result = a.result;
     double* result64 = a.result64;
     void* args[] = {&x, &y, &n, &partials, &ticket, &result, &result64};
-    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args);
+    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args, true);
   }
 };
 

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(THREADS)
                   const float* __restrict__ x, float beta, float* __restrict__ y, int64_t B,
                   float* __restrict__ partials, unsigned* __restrict__ tickets) {
   constexpr int CB = THREADS * VW;
+  pdl_wait();      // the previous kernel on the stream has completed
   const int64_t cb = blockIdx.x, rb = blockIdx.y, RB = gridDim.y;
   const int64_t c0 = cb * CB + (int64_t)threadIdx.x * VW;
   const int64_t r0 = rb * B, r1 = (r0 + B < M) ? r0 + B : M;
@@ -181,7 +182,8 @@ __global__ void __launch_bounds__(THREADS)
 __global__ void __launch_bounds__(256)
     gemv_t_combine(int64_t N, int64_t RB, float alpha, float beta,
                    const float* __restrict__ partials, float* __restrict__ y) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the first pass has finished
   const int lane = threadIdx.x & (kWarp - 1);
   const int64_t W = (int64_t)gridDim.x * (blockDim.x / kWarp);
   for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp; j < N; j += W) {
@@ -319,6 +321,7 @@ __global__ void __launch_bounds__(THREADS + kWarp, 1)
     }
     fence_mbar_init();
   }
+  pdl_wait();      // the previous kernel on the stream has completed
   __syncthreads();
 
   if (threadIdx.x >= THREADS) {
@@ -484,7 +487,8 @@ struct GemvT {
     float* partials = a.ws->partials;
     unsigned* tickets = a.ws->tickets + kTicketBase;
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &B, &partials, &tickets};
-    lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args);
+    lift_status r =
+        launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS), 0, 1, s, args, true);
     if (r != LIFT_OK || PASSES == 1) return r;
     return launch_rows_combine(N, RB, alpha, beta, partials, y, s);
   }
@@ -602,7 +606,7 @@ struct GemvTStaged {
     uint32_t polls = wait_polls();
     void* args[] = {&M, &N, &A, &lda, &x, &B, &partials, &status, &polls};
     lift_status r = launch_config(kernel(), dim3((unsigned)ncb, (unsigned)RB), dim3(THREADS + kWarp),
-                                  smem(), 1, s, args);
+                                  smem(), 1, s, args, true);
     if (r != LIFT_OK) return r;
     return launch_rows_combine(N, RB, a.alpha, a.beta, partials, a.out, s);
   }

@@ -66,6 +66,8 @@ __global__ void __launch_bounds__((WARPS + 1) * kWarp, 1)
     }
     fence_mbar_init();
   }
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the previous kernel on the stream has completed
   __syncthreads();
 
   if (warp == WARPS) {
@@ -207,7 +209,8 @@ struct GemvTma {
       if (rc != LIFT_OK) return rc;
     }
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y, &status, &amap};
-    return launch_config(kernel(), dim3((unsigned)g), dim3((WARPS + 1) * kWarp), smem(), 1, s, args);
+    return launch_config(kernel(), dim3((unsigned)g), dim3((WARPS + 1) * kWarp), smem(), 1, s, args,
+                         true);
   }
 };
 

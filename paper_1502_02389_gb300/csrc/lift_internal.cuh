@@ -93,8 +93,22 @@ void register_mixed(std::vector<Variant>* ops);   // ops[LIFT_OP_*]
 // Occupancy-derived persistent grid: SMs x resident CTAs per SM.
 int64_t persistent_grid(const void* kernel, int threads, size_t smem, int cluster);
 
+// pdl: launch as a programmatic dependent of the kernel before it on the
+// stream (the kernel must execute griddepcontrol.wait before its first
+// global memory access; see pdl_wait).
 lift_status launch_config(const void* kernel, dim3 grid, dim3 block, size_t smem,
-                          int cluster, cudaStream_t s, void** args);
+                          int cluster, cudaStream_t s, void** args, bool pdl = false);
+
+// Programmatic dependent launch across calls.  A kernel launched with the
+// pdl flag may be scheduled while the kernel before it on the stream is
+// still running (once that kernel's CTAs have all executed pdl_trigger or
+// exited); pdl_wait blocks until that kernel has completed and its memory
+// operations are visible, so everything after it is ordered exactly as on a
+// plain stream.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 inline bool aligned(const void* p, int bytes) {
   return (reinterpret_cast<uintptr_t>(p) % static_cast<uintptr_t>(bytes)) == 0;

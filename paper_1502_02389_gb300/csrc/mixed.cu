@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(THREADS)
                  const float* __restrict__ ys, int64_t n, double* __restrict__ partials,
                  unsigned* ticket, float* result, double* result64) {
   constexpr int E = kBlock / THREADS;
+  pdl_wait();      // the previous kernel on the stream has completed
   const int t = threadIdx.x;
   const int64_t G = gridDim.x;
   const int64_t full = n / kBlock;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(THREADS)
     fold_block_guarded<OP, DT, E>(acc, x, y, b * kBlock + (int64_t)t * E, n,
                                   block_scale<OP, DT>(xs, ys, b));
 
+  pdl_trigger();   // streaming done: the next call's first kernel may be scheduled
   const Comp c = block_comp<THREADS>(acc);
   __shared__ bool is_last;
   __shared__ double red64[kWarp];
@@ -316,7 +318,7 @@ struct Mixed {
     float* result = a.result;
     double* result64 = a.result64;
     void* args[] = {&x, &xs, &y, &ys, &n, &partials, &ticket, &result, &result64};
-    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args);
+    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args, true);
   }
 };
 

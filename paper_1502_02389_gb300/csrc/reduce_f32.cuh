@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(THREADS)
   static_assert(V % THREADS == 0 && J >= 1, "tile too small for the CTA");
   __shared__ float red[kWarp];
   __shared__ double red64[kWarp];
+  pdl_wait();   // the previous kernel on the stream has completed
   const int t = threadIdx.x;
   const int64_t full = n / TILE;
   float acc = 0.0f, cmp = 0.0f;
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(THREADS)
     for (int s = 0; s < STAGES; ++s) mbar_init(&full_bar[s], 1);
     fence_mbar_init();
   }
+  pdl_wait();   // the previous kernel on the stream has completed
   __syncthreads();
   auto issue = [&](int64_t k) {
     const int s = static_cast<int>(k % STAGES);
@@ -300,7 +302,8 @@ __global__ void __launch_bounds__(THREADS)
 template <int OP, int FT>
 __global__ void __launch_bounds__(FT)
     combine_kernel(const float* __restrict__ partials, int64_t P, float* result, double* result64) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");   // the first pass has finished
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the first pass has finished
   __shared__ double red64[kWarp];
   const double s = post<OP>(combine_partials<FT>(partials, P, red64));
   if (threadIdx.x == 0) {
@@ -373,7 +376,8 @@ struct ReduceF32 {
     int* status = st->ws.status;
     uint32_t polls = wait_polls();
     void* args[] = {&x, &y, &n, &partials, &ticket, &result, &result64, &status, &polls};
-    lift_status rc = launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), CLUSTER, s, args);
+    lift_status rc =
+        launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), CLUSTER, s, args, true);
     if (rc != LIFT_OK || PASSES == 1) return rc;
     return launch_combine<OP>(partials, g / CLUSTER, a.result, a.result64, s);
   }

@@ -48,6 +48,8 @@ __global__ void __launch_bounds__(THREADS)
     scal_ldg(int64_t n, float alpha, const float* x, float* y) {
   constexpr int J = TILE / VW / THREADS;
   static_assert(J >= 1 && (TILE / VW) % THREADS == 0, "tile too small");
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the previous kernel on the stream has completed
   const int64_t full = n / TILE;
   int64_t tile = blockIdx.x;
   for (; tile < full; tile += gridDim.x) {
@@ -79,6 +81,8 @@ __global__ void __launch_bounds__(THREADS)
     for (int s = 0; s < STAGES; ++s) mbar_init(&full_bar[s], 1);
     fence_mbar_init();
   }
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the previous kernel on the stream has completed
   __syncthreads();
   auto issue = [&](int64_t k) {
     const int s = static_cast<int>(k % STAGES);
@@ -163,10 +167,10 @@ struct Scal {
     int* status = current_state()->ws.status;
     if constexpr (STAGES == 0) {
       void* args[] = {&n, &alpha, &x, &y};
-      return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args);
+      return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args, true);
     } else {
       void* args[] = {&n, &alpha, &x, &y, &status};
-      return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), 1, s, args);
+      return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), smem(), 1, s, args, true);
     }
   }
 };
@@ -202,6 +206,8 @@ __global__ void __launch_bounds__(THREADS)
     axpy_ldg(int64_t n, float alpha, const float* x, float* y) {
   constexpr int J = TILE / VW / THREADS;
   static_assert(J >= 1 && (TILE / VW) % THREADS == 0, "tile too small");
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the previous kernel on the stream has completed
   const int64_t full = n / TILE;
   int64_t tile = blockIdx.x;
   for (; tile < full; tile += gridDim.x) {
@@ -245,7 +251,7 @@ struct Axpy {
     const float* x = static_cast<const float*>(a.x);
     float* y = a.out;
     void* args[] = {&n, &alpha, &x, &y};
-    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args);
+    return launch_config(kernel(), dim3((unsigned)g), dim3(THREADS), 0, 1, s, args, true);
   }
 };
 
@@ -293,6 +299,8 @@ __global__ void __launch_bounds__(WARPS * kWarp)
     gemv_warp(int64_t M, int64_t N, float alpha, const float* __restrict__ A, int64_t lda,
               const float* __restrict__ x, float beta, float* __restrict__ y) {
   constexpr int64_t kChunk = (int64_t)kWarp * VW;
+  pdl_trigger();   // the next call's first kernel may be scheduled (it waits for this one)
+  pdl_wait();      // the previous kernel on the stream has completed
   const int lane = threadIdx.x & (kWarp - 1);
   const int64_t gw = (int64_t)blockIdx.x * WARPS + threadIdx.x / kWarp;
   const int64_t total = (int64_t)gridDim.x * WARPS;
@@ -371,7 +379,7 @@ struct Gemv {
     const float* A = a.A;
     const float* x = static_cast<const float*>(a.x);
     void* args[] = {&M, &N, &alpha, &A, &lda, &x, &beta, &y};
-    return launch_config(kernel(), dim3((unsigned)g), dim3(WARPS * kWarp), 0, 1, s, args);
+    return launch_config(kernel(), dim3((unsigned)g), dim3(WARPS * kWarp), 0, 1, s, args, true);
   }
 };
 
