@@ -41,6 +41,11 @@
  *    to 8 streams of a device; calls on the same stream are ordered by it.
  *    Calls on more than 8 streams at once share slots and can race (and
  *    after 4096 distinct stream handles the assignment starts afresh).
+ *  - Most kernels are launched as programmatic dependents of the kernel
+ *    before them on the stream: their CTAs may be scheduled while that
+ *    kernel still runs, but each waits for it to complete (and for its
+ *    writes to be visible) before touching memory, so calls on one stream
+ *    stay ordered exactly as stream order promises.
  *  - lift_last_error() returns a detail message for the last failure of the
  *    calling thread.
  */
@@ -105,7 +110,8 @@ typedef enum {
  * up to 8 streams may run at the same time.  A CUDA graph keeps the slot of
  * the stream it was captured on.  Must be called (once per device) before
  * any other call on that device, outside CUDA graph capture.  Calling it
- * again is a no-op.
+ * again is a no-op; calls from several threads at once set the device up
+ * once.
  * The first call also reads two environment overrides:
  *   LIFT_POLICY  = fixed | table:<path> | mlp[:<path>] | mlp_tune[:<path>]
  *                  (the learned policies default to the weights file
