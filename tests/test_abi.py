@@ -122,3 +122,16 @@ def test_batch_create_rejects_bad_descriptors_before_any_device_work(lib):
             lift.lift_batch_create([good, d])
         assert e.value.status == lift.ERR_INVALID_ARG, d
         assert "batch op 1" in lift.lib().lift_last_error().decode()
+
+
+def test_fixed_policy_defaults_name_registered_variants(lib):
+    """Each op's FIXED default (kDefaultName in csrc/api.cu, indexed by op
+    id) is a variant of that op: a name that no longer matches would make the
+    FIXED policy fall back silently to the op's first variant."""
+    from paper_1502_02389_gb300 import lift
+    src = open(os.path.join(ROOT, "paper_1502_02389_gb300", "csrc", "api.cu")).read()
+    body = re.search(r"kDefaultName\[LIFT_NUM_OPS\]\s*=\s*\{(.*?)\};", src, re.S).group(1)
+    names = re.findall(r'"([^"]+)"', body)
+    assert len(names) == lift.NUM_OPS
+    for op, name in enumerate(names):
+        assert name in {v["name"] for v in lift.variants(op)}, (lift.OP_NAMES[op], name)
